@@ -1,0 +1,300 @@
+"""Throughput benchmark of the STG-LBM hot path (MLUPS and HBM roofline).
+
+One step = the STG inlet kernel plus the fused stream/collide kernel over the
+whole lattice (with FP64 statistics every 10 steps), i.e. one pass of the
+whole hot path.  Default workload: the Re_tau = 180 channel on a 768x128x192
+D3Q19 FP32 lattice (h = 64, 200 STG modes), inputs resident in HBM, lattice
+(2.9 GB) far larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one independent channel per GPU (weak scaling, no collective on
+the data path).  ``--impl reference`` times the CPU FP64 oracle on the host
+cores instead (bounded sample).  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = {"fp32": 152, "fp16s": 76}  # 19 populations read + 19 written
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("step_kernel.cu", "d3q19.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2205_02774_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(workload, storage):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"lbm_step_kernel_{workload}_{storage}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    mh = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    mt = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    if not mh or not mt or mh.group(1) != _kernel_hash():
+        return None
+    return float(mt.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(workload, storage, steps):
+    """The CPU FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    from workloads import case
+    c = case(workload).with_(storage=storage)
+    sim = oracle.Sim.from_case(c)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    del sim
+    return {"value": c.cells * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{steps} full steps of the {workload} lattice (FP64, OpenMP over z)", "seconds": dt}
+
+
+def run_reference(args):
+    """Reference arm: the CPU FP64 oracle on the host cores.  Each step is one
+    oracle step of a bounded slab of the workload (same ny x nz cross-section,
+    inlet, outlet and walls; nx chosen so that warm-up + timed steps stay
+    within about a minute of CPU time)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from workloads import case
+    full = case(args.workload)
+    budget_cells = 3.0e8  # cell updates over the whole run
+    nx = max(3, min(full.nx, int(budget_cells / ((args.steps + args.warmup) * full.ny * full.nz))))
+    c = full.with_(nx=nx)
+    sim = oracle.Sim.from_case(c)
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    t = time.perf_counter() - t0
+    value = c.cells * args.steps / t / 1e6
+    sample = (f"{args.steps} timed steps (+{args.warmup} warm-up) of a {nx}x{c.ny}x{c.nz} slab of the "
+              f"{args.workload} channel (inlet, outlet, walls, {c.n_modes} STG modes)")
+    line = {"impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "storage": "fp64 (oracle)",
+                                             "sample_cells": c.cells},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2205_02774_gb300 import build
+    build()
+    from paper_2205_02774_gb300.channel import Channel
+    from workloads import case
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    c = case(args.workload).with_(storage=args.storage)
+    ch = Channel.from_case(c, check_every=100, mass_tol=0.5, seed=c.seed + rank)
+    stream = ch.stream
+
+    # warm-up (also initialises graphs, clocks)
+    ch.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ch.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = ch.stats()
+    if st["rc"] != 0:
+        raise RuntimeError(f"channel check failed: {st['error']}")
+
+    # dominant kernel: per-launch device time of the fused step kernel
+    ms_step, ms_inlet = ch.step_timed(min(200, max(20, args.steps // 10)))
+    ch.close()
+    del ch
+    torch.cuda.synchronize()
+
+    # end-to-end through the public API with host buffers
+    e2e = None
+    if rank == 0:
+        prof = c.profile()
+        host_in = sum(a.nbytes for a in (prof.y_c, prof.U, prof.k, prof.eps, prof.R))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ch2 = Channel.from_case(c, check_every=100, mass_tol=0.5)
+        ch2.step(args.steps)
+        st2 = ch2.stats()
+        t1 = time.perf_counter()
+        host_out = 9 * c.nx * c.ny * 8 + 16
+        ch2.close()
+        e2e = {"value": c.cells * args.steps / (t1 - t0) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": host_in / args.steps, "d2h_bytes_per_step": host_out / args.steps,
+               "seconds": t1 - t0, "includes": "create (host profile upload, tables, init, graph capture) + "
+                                               "step(K) + stats (FP64 sums to host) + destroy"}
+        assert st2["rc"] == 0
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = _peaks()
+    bpc = BYTES_PER_CELL[args.storage]
+    achieved = bpc * c.cells / (ms_step * 1e-3) / 1e9
+    value = c.cells * args.steps * ws / (ms * 1e-3) / 1e6
+    traffic = _traffic(args.workload, args.storage)
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "storage": args.storage, "cells": c.cells, "lattice": "D3Q19",
+                   "collision": c.collision, "stg_modes": c.n_modes, "stats_every": c.stats_every,
+                   "l2": "inputs larger than L2 (lattice %.2f GB)" % (2 * 19 * c.cells * bpc / 38 / 1e9),
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "lbm_step_kernel", "kernel_ms": ms_step,
+                     "bytes_per_cell": bpc, "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                     "inlet_kernel_ms": ms_inlet},
+        "hbm_frac_of_step": bpc * c.cells * args.steps / (ms * 1e-3) / 1e9 / peak,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.storage, args.cpu_steps)
+        line["cpu_baseline"].pop("seconds", None)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="channel_768x128x192")
+    ap.add_argument("--storage", choices=["fp32", "fp16s"], default="fp32")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+"""ctypes binding of libstglbm.so, one Python function per C entry point.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  There is no fallback; if the shared library is missing or cannot be
+loaded, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstglbm.so")
+
+STG_OK, STG_ERR_INVALID, STG_ERR_NOMEM, STG_ERR_UNSTABLE, STG_ERR_TIMEOUT, STG_ERR_CUDA = range(6)
+STG_FP32, STG_FP16_SHIFTED = 0, 1
+STG_REGULARIZED, STG_BGK = 0, 1
+STG_BC_X_INLET_OUTLET, STG_BC_X_PERIODIC = 0, 1
+STG_BC_Y_WALLS, STG_BC_Y_PERIODIC = 0, 1
+
+c_double_p = C.POINTER(C.c_double)
+
+
+class stg_domain(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("storage", C.c_int32),
+                ("collision", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32),
+                ("stats_every", C.c_int32), ("check_every", C.c_int32), ("pad0", C.c_int32),
+                ("tau0", C.c_double), ("c_smag", C.c_double), ("force", C.c_double * 3),
+                ("mass_tol", C.c_double)]
+
+
+class stg_rans_profile(C.Structure):
+    _fields_ = [("n_fv", C.c_int32), ("pad0", C.c_int32), ("y_c", c_double_p), ("U", c_double_p),
+                ("k", c_double_p), ("eps", c_double_p), ("R", c_double_p), ("U_bulk", C.c_double),
+                ("nu_phys", C.c_double), ("h_phys", C.c_double), ("mach_target", C.c_double)]
+
+
+class stg_params(C.Structure):
+    _fields_ = [("n_modes", C.c_int32), ("pad0", C.c_int32), ("C_l", C.c_double), ("alpha", C.c_double),
+                ("T_filter", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class stg_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class stg_stats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("n_samples", C.c_int64), ("mass", C.c_double), ("mass0", C.c_double),
+                ("mean_sum", c_double_p), ("rey_sum", c_double_p)]
+
+
+class stg_info(C.Structure):
+    _fields_ = [("c_x", C.c_double), ("c_t", C.c_double), ("U_b", C.c_double), ("max_le", C.c_double),
+                ("k_min", C.c_double), ("k_max", C.c_double), ("a_filter", C.c_double),
+                ("n_modes", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+_SIGNATURES = {
+    "stg_lbm_create": (C.c_int, [C.POINTER(stg_domain), C.POINTER(stg_rans_profile), C.POINTER(stg_params),
+                                 C.c_uint64, C.POINTER(stg_allocator), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "stg_lbm_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "stg_lbm_step_timed": (C.c_int, [C.c_void_p, C.c_int64, c_double_p, c_double_p]),
+    "stg_lbm_stats": (C.c_int, [C.c_void_p, C.POINTER(stg_stats)]),
+    "stg_lbm_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "stg_lbm_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int64]),
+    "stg_lbm_get_inlet": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "stg_lbm_device_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+    "stg_lbm_info": (C.c_int, [C.c_void_p, C.POINTER(stg_info)]),
+    "stg_lbm_destroy": (None, [C.c_void_p]),
+    "stg_lbm_last_error": (C.c_char_p, [C.c_void_p]),
+    "stg_mode_draws": (C.c_int, [C.c_uint64, C.c_int32, c_double_p]),
+    "stg_lbm_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libstglbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libstglbm.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class StgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def _check(rc, handle=None):
+    if rc != STG_OK:
+        msg = lib().stg_lbm_last_error(handle)
+        raise StgError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# ---------------------------------------------------------------- raw entry points
+def stg_lbm_create(domain, rans, params, seed, allocator=None, stream=0):
+    h = C.c_void_p()
+    rc = lib().stg_lbm_create(C.byref(domain), C.byref(rans) if rans is not None else None,
+                              C.byref(params) if params is not None else None, seed,
+                              C.byref(allocator) if allocator is not None else None, C.c_void_p(stream),
+                              C.byref(h))
+    _check(rc, None)
+    return h
+
+
+def stg_lbm_step(h, n):
+    return _check(lib().stg_lbm_step(h, n), h)
+
+
+def stg_lbm_step_timed(h, n):
+    a = C.c_double()
+    b = C.c_double()
+    _check(lib().stg_lbm_step_timed(h, n, C.byref(a), C.byref(b)), h)
+    return a.value, b.value
+
+
+def stg_lbm_stats(h, mean_sum=None, rey_sum=None):
+    s = stg_stats()
+    s.mean_sum = mean_sum.ctypes.data_as(c_double_p) if mean_sum is not None else None
+    s.rey_sum = rey_sum.ctypes.data_as(c_double_p) if rey_sum is not None else None
+    rc = lib().stg_lbm_stats(h, C.byref(s))
+    return rc, s
+
+
+def stg_lbm_get_state(h, out):
+    return _check(lib().stg_lbm_get_state(h, C.c_void_p(out.ctypes.data), out.nbytes), h)
+
+
+def stg_lbm_set_state(h, arr, step=0):
+    return _check(lib().stg_lbm_set_state(h, C.c_void_p(arr.ctypes.data), arr.nbytes, step), h)
+
+
+def stg_lbm_get_inlet(h, out):
+    return _check(lib().stg_lbm_get_inlet(h, out.ctypes.data_as(C.POINTER(C.c_float))), h)
+
+
+def stg_lbm_device_state(h):
+    p = C.c_void_p()
+    u = C.c_void_p()
+    _check(lib().stg_lbm_device_state(h, C.byref(p), C.byref(u)), h)
+    return p.value, u.value
+
+
+def stg_lbm_info(h):
+    i = stg_info()
+    _check(lib().stg_lbm_info(h, C.byref(i)), h)
+    return i
+
+
+def stg_lbm_destroy(h):
+    lib().stg_lbm_destroy(h)
+
+
+def stg_lbm_last_error(h=None):
+    m = lib().stg_lbm_last_error(h)
+    return m.decode() if m else ""
+
+
+def stg_mode_draws(seed, n):
+    out = np.zeros(4 * n)
+    _check(lib().stg_mode_draws(seed, n, out.ctypes.data_as(c_double_p)))
+    return out
+
+
+def stg_lbm_version():
+    return lib().stg_lbm_version().decode()

@@ -1,0 +1,736 @@
+// Host side of libstglbm.so: argument checks, the FP64 inlet setup
+// (Algorithm 1, LBM section steps 1-4), device state, CUDA-graph step loop,
+// readback and error reporting.  Declarations and conventions: stg_lbm.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+#include "stg_lbm.h"
+
+using stg::StepCtl;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kCs = 0.57735026918962576451;  // sqrt(1/3)
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct stg_lbm {
+    stg_domain d{};
+    stg_params p{};
+    bool inout = false;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    stg_allocator alloc{};
+    bool has_alloc = false;
+    std::vector<std::pair<void *, size_t>> allocs;
+    size_t P = 0, elem = 4;
+    void *lat[2] = {nullptr, nullptr};
+    float *ubc = nullptr, *uf = nullptr;
+    float *A = nullptr, *B = nullptr, *SQ = nullptr, *sig = nullptr, *a6 = nullptr, *u_int = nullptr;
+    double *phi = nullptr, *omg = nullptr;
+    int N = 0;
+    float a_filter = 0.f;
+    StepCtl *ctl = nullptr;
+    double *stat_mean = nullptr, *stat_rey = nullptr;
+    double *mass_partial = nullptr, *mass_out = nullptr;
+    unsigned *mass_counter = nullptr;
+    double *m_partial = nullptr, *m_out = nullptr;
+    unsigned *m_counter = nullptr;
+    double *h_pinned = nullptr;  // [0]: last checked mass
+    cudaEvent_t ev_check = nullptr, ev_done = nullptr;
+    bool check_pending = false;
+    int64_t t = 0, t0_stats = 0;
+    double mass0 = 0.0;
+    int sticky = STG_OK;
+    std::string err;
+    cudaGraphExec_t g_single[2] = {nullptr, nullptr};
+    cudaGraphExec_t g_block[2] = {nullptr, nullptr};
+    int block_steps = 16;
+    stg_info info{};
+    double timeout_s = 900.0;
+};
+
+namespace {
+
+int fail(stg_lbm *h, int code, const std::string &msg)
+{
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(stg_lbm *h, cudaError_t e, const char *what)
+{
+    return fail(h, STG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);  \
+    } while (0)
+
+void *dalloc(stg_lbm *h, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void *p = nullptr;
+    if (h->has_alloc) {
+        p = h->alloc.alloc(bytes, h->alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        h->allocs.emplace_back(p, bytes);
+        h->info.device_bytes += (int64_t)bytes;
+    }
+    return p;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): Weyl increment + 64-bit finaliser.
+void splitmix_uniform(uint64_t seed, int32_t n, double *out)
+{
+    uint64_t state = seed;
+    for (int32_t i = 0; i < n; ++i) {
+        state += 0x9E3779B97F4A7C15ULL;
+        uint64_t z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        out[i] = (double)(z >> 11) * 0x1.0p-53;
+    }
+}
+
+// Piecewise-linear profile through (0, lo), the FV centres, (2h, hi).
+struct Interp {
+    const double *yc;
+    int n;
+    double top;
+    double at(const double *v, int stride, int comp, double lo, double hi, double y) const
+    {
+        if (y <= yc[0]) return lo + (v[comp] - lo) * (y / yc[0]);
+        if (y >= yc[n - 1]) {
+            const double span = top - yc[n - 1];
+            const double s = span > 0 ? (y - yc[n - 1]) / span : 0.0;
+            return v[(size_t)(n - 1) * stride + comp] + (hi - v[(size_t)(n - 1) * stride + comp]) * s;
+        }
+        int lo_i = 0, hi_i = n - 1;  // bisection: yc[lo_i] <= y < yc[hi_i]
+        while (hi_i - lo_i > 1) {
+            const int mid = (lo_i + hi_i) / 2;
+            if (yc[mid] <= y) lo_i = mid;
+            else hi_i = mid;
+        }
+        const double s = (y - yc[lo_i]) / (yc[hi_i] - yc[lo_i]);
+        const double a = v[(size_t)lo_i * stride + comp], b = v[(size_t)hi_i * stride + comp];
+        return a + (b - a) * s;
+    }
+};
+
+double wrap2pi(double v)
+{
+    v = std::fmod(v, 2.0 * kPi);
+    return v < 0.0 ? v + 2.0 * kPi : v;
+}
+
+// Inlet tables: Algorithm 1, LBM section steps 1-4.
+int build_inlet(stg_lbm *h, const stg_rans_profile *r, uint64_t seed)
+{
+    const int ny = h->d.ny, nz = h->d.nz;
+    const stg_rans_profile &R = *r;
+    // unit conversion, eqs. (c_factor), (u_transfer), (lbe-nu), (ma-eq)
+    const double c_x = 2.0 * R.h_phys / ny;
+    double Umax = 0.0;
+    for (int i = 0; i < R.n_fv; ++i) Umax = std::max(Umax, R.U[i]);
+    double c_t;
+    if (R.mach_target > 0.0) {
+        if (!(Umax > 0.0)) return fail(h, STG_ERR_INVALID, "mach_target needs max(U) > 0");
+        c_t = R.mach_target * kCs * c_x / Umax;
+    } else {
+        c_t = (h->d.tau0 - 0.5) / 3.0 * c_x * c_x / R.nu_phys;
+    }
+    const double su = c_t / c_x;
+    if (Umax * su / kCs >= 0.1)
+        return fail(h, STG_ERR_INVALID, "lattice Mach number of the RANS maximum velocity is >= 0.1");
+    h->info.c_x = c_x;
+    h->info.c_t = c_t;
+    h->info.U_b = R.U_bulk * su;
+
+    Interp ip{R.y_c, R.n_fv, 2.0 * R.h_phys};
+    std::vector<double> u_int(ny), R6(6 * (size_t)ny), le(ny), leta(ny), lcut(ny);
+    double max_le = 0.0, max_kcut = 0.0;
+    for (int j = 0; j < ny; ++j) {
+        const double y = (j + 0.5) * c_x;
+        const double U = ip.at(R.U, 1, 0, 0.0, 0.0, y);
+        const double k = ip.at(R.k, 1, 0, 0.0, 0.0, y);
+        const double eps = ip.at(R.eps, 1, 0, R.eps[0], R.eps[R.n_fv - 1], y);
+        for (int c = 0; c < 6; ++c) R6[6 * (size_t)j + c] = ip.at(R.R, 6, c, 0.0, 0.0, y) * su * su;
+        u_int[j] = U * su;
+        // l_e = min(2 d_w, C_l l_t), l_t = k^{3/2}/eps; l_eta = (nu^3/eps)^{1/4}; lattice units
+        const double dw = std::min(y, 2.0 * R.h_phys - y);
+        const double lt = eps > 0.0 ? std::pow(std::max(k, 0.0), 1.5) / eps : 0.0;
+        le[j] = std::min(2.0 * dw, h->p.C_l * lt) / c_x;
+        leta[j] = eps > 0.0 ? std::pow(R.nu_phys * R.nu_phys * R.nu_phys / eps, 0.25) / c_x : 0.0;
+        // eq. (lcut) with the lattice spacings (1, 1, 1)
+        lcut[j] = 2.0 * std::min(std::max(1.0, 0.3) + 0.1 * dw / c_x, 1.0);
+        max_le = std::max(max_le, le[j]);
+        max_kcut = std::max(max_kcut, 2.0 * kPi / lcut[j]);
+    }
+    h->info.max_le = max_le;
+    int N = 0;
+    std::vector<double> kn, dk, phi, omg;
+    std::vector<float> sig, A, B;
+    if (max_le > 0.0) {
+        const double kmin = kPi / max_le, kmax = 1.5 * max_kcut;
+        h->info.k_min = kmin;
+        h->info.k_max = kmax;
+        N = h->p.n_modes > 0 ? h->p.n_modes
+                             : (int)std::ceil(std::log(kmax / kmin) / std::log(1.0 + h->p.alpha) + 1.0);
+        if (N < 1 || N > 100000) return fail(h, STG_ERR_INVALID, "mode count out of range");
+        const double ratio = N > 1 ? std::pow(kmax / kmin, 1.0 / (N - 1)) : 1.0;
+        kn.resize(N);
+        dk.resize(N);
+        for (int n = 0; n < N; ++n) {
+            kn[n] = kmin * std::pow(ratio, (double)n);
+            dk[n] = N > 1 ? kn[n] * (1.0 - 1.0 / ratio) : 1.0;
+        }
+        std::vector<double> u(4 * (size_t)N);
+        splitmix_uniform(seed, 4 * N, u.data());
+        sig.resize(3 * (size_t)N);
+        phi.resize(N);
+        omg.resize(N);
+        A.resize((size_t)N * ny);
+        B.resize((size_t)N * nz);
+        for (int n = 0; n < N; ++n) {
+            // eq. (dn): Phi, Theta = arccos(1 - 2 gamma), eta, phi
+            const double Phi = 2.0 * kPi * u[4 * n + 0];
+            const double Th = std::acos(1.0 - 2.0 * u[4 * n + 1]);
+            const double eta = 2.0 * kPi * u[4 * n + 2];
+            phi[n] = 2.0 * kPi * u[4 * n + 3];
+            const double st = std::sin(Th), ct = std::cos(Th), sp = std::sin(Phi), cp = std::cos(Phi);
+            const double se = std::sin(eta), ce = std::cos(eta);
+            const double dx = st * cp, dy = st * sp, dz = ct;
+            sig[3 * n + 0] = (float)(cp * ct * ce - sp * se);
+            sig[3 * n + 1] = (float)(sp * ct * ce + cp * se);
+            sig[3 * n + 2] = (float)(-st * ce);
+            // eq. (psu) at x = 0: phase advance -2 pi d_x U_b / max l_e per step
+            omg[n] = -2.0 * kPi * dx * h->info.U_b / max_le;
+            for (int j = 0; j < ny; ++j) A[(size_t)n * ny + j] = (float)wrap2pi(kn[n] * dy * (j + 0.5));
+            for (int k = 0; k < nz; ++k) B[(size_t)n * nz + k] = (float)wrap2pi(kn[n] * dz * k);
+        }
+    }
+    h->N = N;
+    h->info.n_modes = N;
+    h->a_filter = h->p.T_filter > 0.0 ? (float)std::exp(-1.0 / h->p.T_filter) : 0.0f;
+    h->info.a_filter = h->a_filter;
+
+    // device tables
+    const size_t Nn = (size_t)std::max(N, 1);
+    h->A = (float *)dalloc(h, sizeof(float) * Nn * ny);
+    h->B = (float *)dalloc(h, sizeof(float) * Nn * nz);
+    h->SQ = (float *)dalloc(h, sizeof(float) * Nn * ny);
+    h->sig = (float *)dalloc(h, sizeof(float) * 3 * Nn);
+    h->phi = (double *)dalloc(h, sizeof(double) * Nn);
+    h->omg = (double *)dalloc(h, sizeof(double) * Nn);
+    h->a6 = (float *)dalloc(h, sizeof(float) * 6 * ny);
+    h->u_int = (float *)dalloc(h, sizeof(float) * ny);
+    double *dR6 = (double *)dalloc(h, sizeof(double) * 6 * ny);
+    double *dle = (double *)dalloc(h, sizeof(double) * 3 * ny);
+    double *dkn = (double *)dalloc(h, sizeof(double) * 2 * Nn);
+    if (!h->A || !h->B || !h->SQ || !h->sig || !h->phi || !h->omg || !h->a6 || !h->u_int || !dR6 || !dle || !dkn)
+        return fail(h, STG_ERR_NOMEM, "device allocation of the inlet tables failed");
+    std::vector<float> uf(ny);
+    for (int j = 0; j < ny; ++j) uf[j] = (float)u_int[j];
+    std::vector<double> lens(3 * (size_t)ny);
+    std::copy(le.begin(), le.end(), lens.begin());
+    std::copy(leta.begin(), leta.end(), lens.begin() + ny);
+    std::copy(lcut.begin(), lcut.end(), lens.begin() + 2 * ny);
+    CK(cudaMemcpy(h->u_int, uf.data(), sizeof(float) * ny, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dR6, R6.data(), sizeof(double) * 6 * ny, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dle, lens.data(), sizeof(double) * 3 * ny, cudaMemcpyHostToDevice));
+    if (N > 0) {
+        std::vector<double> kd(2 * (size_t)N);
+        std::copy(kn.begin(), kn.end(), kd.begin());
+        std::copy(dk.begin(), dk.end(), kd.begin() + N);
+        CK(cudaMemcpy(dkn, kd.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->A, A.data(), sizeof(float) * A.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->B, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->sig, sig.data(), sizeof(float) * sig.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->phi, phi.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->omg, omg.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    }
+    CK(stg::launch_setup_nodes(ny, N, dR6, dle, dle + ny, dle + 2 * ny, dkn, dkn + Nn, h->a6, h->SQ, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return STG_OK;
+}
+
+stg::StepArgs step_args(const stg_lbm *h, int parity)
+{
+    stg::StepArgs a{};
+    a.src = h->lat[parity];
+    a.dst = h->lat[parity ^ 1];
+    a.nx = h->d.nx;
+    a.ny = h->d.ny;
+    a.nz = h->d.nz;
+    a.P = (unsigned)h->P;
+    a.bc_x = h->d.bc_x;
+    a.bc_y = h->d.bc_y;
+    a.tau0 = (float)h->d.tau0;
+    a.kq = (float)(18.0 * std::sqrt(2.0) * h->d.c_smag);
+    a.Fx = (float)h->d.force[0];
+    a.Fy = (float)h->d.force[1];
+    a.Fz = (float)h->d.force[2];
+    a.has_force = (h->d.force[0] != 0.0 || h->d.force[1] != 0.0 || h->d.force[2] != 0.0);
+    a.ubc = h->ubc;
+    a.ctl = h->ctl;
+    a.parity = parity;
+    a.stats_every = h->d.stats_every;
+    a.check_every = h->d.check_every;
+    a.stat_mean = h->stat_mean;
+    a.stat_rey = h->stat_rey;
+    a.mass_partial = h->mass_partial;
+    a.mass_counter = h->mass_counter;
+    a.mass_out = h->mass_out;
+    return a;
+}
+
+stg::InletArgs inlet_args(const stg_lbm *h, int parity)
+{
+    stg::InletArgs a{};
+    a.ny = h->d.ny;
+    a.nz = h->d.nz;
+    a.N = h->N;
+    a.A = h->A;
+    a.B = h->B;
+    a.SQ = h->SQ;
+    a.sig = h->sig;
+    a.phi = h->phi;
+    a.omg = h->omg;
+    a.a6 = h->a6;
+    a.u_int = h->u_int;
+    a.a_filter = h->a_filter;
+    a.uf = h->uf;
+    a.ubc = h->ubc;
+    a.ctl = h->ctl;
+    a.parity = parity;
+    return a;
+}
+
+cudaError_t enqueue_step(stg_lbm *h, int parity)
+{
+    cudaError_t e = cudaSuccess;
+    if (h->inout) {
+        e = stg::launch_inlet(inlet_args(h, parity), h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, h->stream);
+}
+
+int capture(stg_lbm *h, int parity, int steps, cudaGraphExec_t *out)
+{
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < steps && e == cudaSuccess; ++s) e = enqueue_step(h, (parity + s) & 1);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch during capture");
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    return STG_OK;
+}
+
+int wait_stream(stg_lbm *h)
+{
+    CK(cudaEventRecord(h->ev_done, h->stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(h->ev_done);
+        if (e == cudaSuccess) return STG_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(h, e, "cudaEventQuery");
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > h->timeout_s) return fail(h, STG_ERR_TIMEOUT, "timed out waiting for the device");
+        std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 5 : 200));
+    }
+}
+
+// Evaluate the last completed mass check (non-blocking).
+int poll_check(stg_lbm *h)
+{
+    if (!h->check_pending) return STG_OK;
+    cudaError_t e = cudaEventQuery(h->ev_check);
+    if (e == cudaErrorNotReady) return STG_OK;
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventQuery");
+    h->check_pending = false;
+    const double m = h->h_pinned[0];
+    if (!std::isfinite(m)) {
+        h->sticky = STG_ERR_UNSTABLE;
+        return fail(h, STG_ERR_UNSTABLE, "non-finite mass at the last check");
+    }
+    if (h->d.mass_tol > 0.0 && std::fabs(m / h->mass0 - 1.0) > h->d.mass_tol) {
+        h->sticky = STG_ERR_UNSTABLE;
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "mass drift %.3e exceeds %.3e", m / h->mass0 - 1.0, h->d.mass_tol);
+        return fail(h, STG_ERR_UNSTABLE, buf);
+    }
+    return STG_OK;
+}
+
+int compute_mass(stg_lbm *h, double *out)
+{
+    stg::MassArgs m{};
+    m.src = h->lat[h->t & 1];
+    m.P = (unsigned)h->P;
+    m.storage = h->d.storage;
+    m.partial = h->m_partial;
+    m.counter = h->m_counter;
+    m.out = h->m_out;
+    CK(stg::launch_mass(m, h->stream));
+    CK(cudaMemcpyAsync(h->h_pinned + 1, h->m_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    *out = h->h_pinned[1];
+    return STG_OK;
+}
+
+int reset_counters(stg_lbm *h, int64_t step)
+{
+    StepCtl c{};
+    c.t[step & 1] = step;
+    c.t[(step + 1) & 1] = step;
+    c.t0_filter = step;
+    CK(cudaMemcpyAsync(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
+    const size_t m = (size_t)h->d.nx * h->d.ny;
+    CK(cudaMemsetAsync(h->stat_mean, 0, sizeof(double) * 3 * m, h->stream));
+    CK(cudaMemsetAsync(h->stat_rey, 0, sizeof(double) * 6 * m, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->t = step;
+    h->t0_stats = step;
+    h->check_pending = false;
+    h->sticky = STG_OK;
+    return STG_OK;
+}
+
+void release(stg_lbm *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int p = 0; p < 2; ++p) {
+        if (h->g_single[p]) cudaGraphExecDestroy(h->g_single[p]);
+        if (h->g_block[p]) cudaGraphExecDestroy(h->g_block[p]);
+    }
+    for (auto &a : h->allocs) {
+        if (h->has_alloc) h->alloc.free(a.first, a.second, h->alloc.ctx);
+        else cudaFree(a.first);
+    }
+    h->allocs.clear();
+    if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    if (h->ev_check) cudaEventDestroy(h->ev_check);
+    if (h->ev_done) cudaEventDestroy(h->ev_done);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int validate(const stg_domain *d, const stg_rans_profile *r, const stg_params *p)
+{
+    if (!d) return fail(nullptr, STG_ERR_INVALID, "domain is NULL");
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return fail(nullptr, STG_ERR_INVALID, "lattice sizes must be >= 1");
+    const double cells = (double)d->nx * d->ny * d->nz;
+    if (cells > 2147483647.0) return fail(nullptr, STG_ERR_INVALID, "more than 2^31-1 cells");
+    if (d->ny > 65535) return fail(nullptr, STG_ERR_INVALID, "ny must be <= 65535");
+    if (d->storage != STG_FP32 && d->storage != STG_FP16_SHIFTED) return fail(nullptr, STG_ERR_INVALID, "bad storage");
+    if (d->collision != STG_REGULARIZED && d->collision != STG_BGK) return fail(nullptr, STG_ERR_INVALID, "bad collision");
+    if (d->bc_x != STG_BC_X_INLET_OUTLET && d->bc_x != STG_BC_X_PERIODIC) return fail(nullptr, STG_ERR_INVALID, "bad bc_x");
+    if (d->bc_y != STG_BC_Y_WALLS && d->bc_y != STG_BC_Y_PERIODIC) return fail(nullptr, STG_ERR_INVALID, "bad bc_y");
+    if (!(d->tau0 > 0.5) || !std::isfinite(d->tau0)) return fail(nullptr, STG_ERR_INVALID, "tau0 must be > 1/2");
+    if (!(d->c_smag >= 0.0) || !std::isfinite(d->c_smag)) return fail(nullptr, STG_ERR_INVALID, "c_smag must be >= 0");
+    if (d->stats_every < 0 || d->check_every < 0) return fail(nullptr, STG_ERR_INVALID, "negative cadence");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(d->force[a])) return fail(nullptr, STG_ERR_INVALID, "non-finite force");
+    if (d->bc_x == STG_BC_X_INLET_OUTLET) {
+        if (d->nx < 3) return fail(nullptr, STG_ERR_INVALID, "inlet/outlet needs nx >= 3");
+        if (!r || !p) return fail(nullptr, STG_ERR_INVALID, "inlet/outlet needs a RANS profile and STG parameters");
+        if (r->n_fv < 2 || !r->y_c || !r->U || !r->k || !r->eps || !r->R)
+            return fail(nullptr, STG_ERR_INVALID, "RANS profile needs n_fv >= 2 and all arrays");
+        if (!(r->h_phys > 0.0) || !(r->nu_phys > 0.0) || !(r->mach_target >= 0.0) || !std::isfinite(r->U_bulk))
+            return fail(nullptr, STG_ERR_INVALID, "RANS scalars out of range");
+        for (int i = 0; i < r->n_fv; ++i) {
+            if (!(r->y_c[i] > 0.0 && r->y_c[i] < 2.0 * r->h_phys) || (i > 0 && !(r->y_c[i] > r->y_c[i - 1])))
+                return fail(nullptr, STG_ERR_INVALID, "y_c must increase strictly inside (0, 2 h_phys)");
+            if (!std::isfinite(r->U[i]) || !(r->k[i] >= 0.0) || !(r->eps[i] >= 0.0))
+                return fail(nullptr, STG_ERR_INVALID, "RANS U, k, eps must be finite, k and eps >= 0");
+            for (int c = 0; c < 6; ++c)
+                if (!std::isfinite(r->R[6 * (size_t)i + c])) return fail(nullptr, STG_ERR_INVALID, "non-finite R");
+        }
+        if (!(p->C_l > 0.0) || !(p->alpha > 0.0) || !(p->T_filter >= 0.0) || p->n_modes < 0)
+            return fail(nullptr, STG_ERR_INVALID, "STG parameters out of range");
+    }
+    return STG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const stg_params *stgp, uint64_t seed,
+                   const stg_allocator *alloc, void *stream, stg_lbm **out)
+{
+    if (!out) return fail(nullptr, STG_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int rc = validate(domain, rans, stgp);
+    if (rc) return rc;
+    stg_lbm *h = new stg_lbm();
+    h->d = *domain;
+    if (stgp) h->p = *stgp;
+    h->inout = domain->bc_x == STG_BC_X_INLET_OUTLET;
+    if (alloc && alloc->alloc && alloc->free) {
+        h->alloc = *alloc;
+        h->has_alloc = true;
+    }
+    auto bail = [&](int code) {
+        g_create_error = h->err;
+        release(h);
+        return code;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        h->err = "no CUDA device";
+        return bail(STG_ERR_CUDA);
+    }
+    if (stream) {
+        h->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            h->err = "cudaStreamCreate failed";
+            return bail(STG_ERR_CUDA);
+        }
+        h->own_stream = true;
+    }
+    if (cudaEventCreateWithFlags(&h->ev_check, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(&h->h_pinned, 4 * sizeof(double)) != cudaSuccess) {
+        h->err = "event / pinned allocation failed";
+        return bail(STG_ERR_CUDA);
+    }
+    const int nx = domain->nx, ny = domain->ny, nz = domain->nz;
+    h->P = (size_t)nx * ny * nz;
+    h->elem = domain->storage == STG_FP32 ? 4 : 2;
+    h->lat[0] = dalloc(h, 19 * h->P * h->elem);
+    h->lat[1] = dalloc(h, 19 * h->P * h->elem);
+    h->ubc = (float *)dalloc(h, sizeof(float) * 3 * (size_t)ny * nz);
+    h->uf = (float *)dalloc(h, sizeof(float) * 3 * (size_t)ny * nz);
+    h->ctl = (StepCtl *)dalloc(h, sizeof(StepCtl));
+    h->stat_mean = (double *)dalloc(h, sizeof(double) * 3 * (size_t)nx * ny);
+    h->stat_rey = (double *)dalloc(h, sizeof(double) * 6 * (size_t)nx * ny);
+    h->mass_partial = (double *)dalloc(h, sizeof(double) * stg::step_grid_blocks(nx, ny));
+    h->mass_counter = (unsigned *)dalloc(h, sizeof(unsigned) * 4);
+    h->mass_out = (double *)dalloc(h, sizeof(double) * 2);
+    h->m_partial = (double *)dalloc(h, sizeof(double) * stg::mass_grid_blocks());
+    h->m_counter = (unsigned *)dalloc(h, sizeof(unsigned) * 4);
+    h->m_out = (double *)dalloc(h, sizeof(double) * 2);
+    if (!h->lat[0] || !h->lat[1] || !h->ubc || !h->uf || !h->ctl || !h->stat_mean || !h->stat_rey ||
+        !h->mass_partial || !h->mass_counter || !h->mass_out || !h->m_partial || !h->m_counter || !h->m_out) {
+        h->err = "device allocation failed";
+        return bail(STG_ERR_NOMEM);
+    }
+    cudaError_t e = cudaSuccess;
+    e = cudaMemsetAsync(h->mass_counter, 0, sizeof(unsigned) * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->m_counter, 0, sizeof(unsigned) * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->mass_out, 0, sizeof(double) * 2, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ubc, 0, sizeof(float) * 3 * (size_t)ny * nz, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->uf, 0, sizeof(float) * 3 * (size_t)ny * nz, h->stream);
+    if (e != cudaSuccess) {
+        cuda_fail(h, e, "cudaMemsetAsync");
+        return bail(STG_ERR_CUDA);
+    }
+    if (h->inout) {
+        rc = build_inlet(h, rans, seed);
+        if (rc) return bail(rc);
+    }
+    e = stg::launch_init_equilibrium(h->lat[0], domain->storage, nx, ny, nz, h->inout ? h->u_int : nullptr,
+                                     h->stream);
+    if (e != cudaSuccess) {
+        cuda_fail(h, e, "init kernel");
+        return bail(STG_ERR_CUDA);
+    }
+    rc = reset_counters(h, 0);
+    if (rc) return bail(rc);
+    rc = compute_mass(h, &h->mass0);
+    if (rc) return bail(rc);
+    for (int p = 0; p < 2 && rc == STG_OK; ++p) {
+        rc = capture(h, p, 1, &h->g_single[p]);
+        if (rc == STG_OK) rc = capture(h, p, h->block_steps, &h->g_block[p]);
+    }
+    if (rc) return bail(rc);
+    *out = h;
+    return STG_OK;
+}
+
+int stg_lbm_step(stg_lbm *h, int64_t n)
+{
+    if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
+    if (n < 0) return fail(h, STG_ERR_INVALID, "negative step count");
+    int rc = poll_check(h);
+    if (rc) return rc;
+    if (h->sticky) return fail(h, h->sticky, "an earlier check failed; reset the state first");
+    while (n > 0) {
+        cudaGraphExec_t g;
+        int k;
+        if (n >= h->block_steps) {
+            g = h->g_block[h->t & 1];
+            k = h->block_steps;
+        } else {
+            g = h->g_single[h->t & 1];
+            k = 1;
+        }
+        CK(cudaGraphLaunch(g, h->stream));
+        h->t += k;
+        n -= k;
+    }
+    if (h->d.check_every > 0) {
+        CK(cudaMemcpyAsync(h->h_pinned, h->mass_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaEventRecord(h->ev_check, h->stream));
+        h->check_pending = true;
+    }
+    return STG_OK;
+}
+
+int stg_lbm_step_timed(stg_lbm *h, int64_t n, double *ms_step, double *ms_inlet)
+{
+    if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
+    if (n < 1 || n > 4096) return fail(h, STG_ERR_INVALID, "step_timed needs 1 <= n <= 4096");
+    if (h->sticky) return fail(h, h->sticky, "an earlier check failed; reset the state first");
+    std::vector<cudaEvent_t> ev(3 * (size_t)n, nullptr);
+    int rc = STG_OK;
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) rc = fail(h, STG_ERR_CUDA, "cudaEventCreate");
+    for (int64_t s = 0; s < n && rc == STG_OK; ++s) {
+        const int parity = (int)(h->t & 1);
+        cudaError_t e = cudaEventRecord(ev[3 * s], h->stream);
+        if (e == cudaSuccess && h->inout) e = stg::launch_inlet(inlet_args(h, parity), h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], h->stream);
+        if (e == cudaSuccess) e = stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "timed step launch");
+        else h->t += 1;
+    }
+    if (rc == STG_OK) rc = wait_stream(h);
+    double sum_s = 0.0, sum_i = 0.0;
+    if (rc == STG_OK) {
+        for (int64_t s = 0; s < n; ++s) {
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
+            cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]);
+            sum_i += a;
+            sum_s += b;
+        }
+    }
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+    if (rc) return rc;
+    if (ms_step) *ms_step = sum_s / (double)n;
+    if (ms_inlet) *ms_inlet = sum_i / (double)n;
+    return STG_OK;
+}
+
+int stg_lbm_stats(stg_lbm *h, stg_stats *out)
+{
+    if (!h || !out) return fail(h, STG_ERR_INVALID, "NULL argument");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    rc = poll_check(h);
+    const size_t m = (size_t)h->d.nx * h->d.ny;
+    if (out->mean_sum) CK(cudaMemcpy(out->mean_sum, h->stat_mean, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost));
+    if (out->rey_sum) CK(cudaMemcpy(out->rey_sum, h->stat_rey, sizeof(double) * 6 * m, cudaMemcpyDeviceToHost));
+    out->step = h->t;
+    const int64_t k = h->d.stats_every;
+    out->n_samples = k > 0 ? (h->t / k - h->t0_stats / k) : 0;
+    out->mass0 = h->mass0;
+    double mass = 0.0;
+    int rc2 = compute_mass(h, &mass);
+    if (rc2) return rc2;
+    out->mass = mass;
+    if (rc) return rc;
+    if (!std::isfinite(mass)) {
+        h->sticky = STG_ERR_UNSTABLE;
+        return fail(h, STG_ERR_UNSTABLE, "non-finite mass");
+    }
+    return h->sticky;
+}
+
+int stg_lbm_get_state(stg_lbm *h, void *host, size_t bytes)
+{
+    if (!h || !host) return fail(h, STG_ERR_INVALID, "NULL argument");
+    if (bytes != 19 * h->P * h->elem) return fail(h, STG_ERR_INVALID, "state size mismatch");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    CK(cudaMemcpy(host, h->lat[h->t & 1], bytes, cudaMemcpyDeviceToHost));
+    return STG_OK;
+}
+
+int stg_lbm_set_state(stg_lbm *h, const void *host, size_t bytes, int64_t step)
+{
+    if (!h || !host) return fail(h, STG_ERR_INVALID, "NULL argument");
+    if (bytes != 19 * h->P * h->elem) return fail(h, STG_ERR_INVALID, "state size mismatch");
+    if (step < 0) return fail(h, STG_ERR_INVALID, "negative step");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    CK(cudaMemcpy(h->lat[step & 1], host, bytes, cudaMemcpyHostToDevice));
+    rc = reset_counters(h, step);
+    if (rc) return rc;
+    return compute_mass(h, &h->mass0);
+}
+
+int stg_lbm_get_inlet(stg_lbm *h, float *host_u)
+{
+    if (!h || !host_u) return fail(h, STG_ERR_INVALID, "NULL argument");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    CK(cudaMemcpy(host_u, h->ubc, sizeof(float) * 3 * (size_t)h->d.ny * h->d.nz, cudaMemcpyDeviceToHost));
+    return STG_OK;
+}
+
+int stg_lbm_device_state(stg_lbm *h, void **pops, float **inlet_u)
+{
+    if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
+    if (pops) *pops = h->lat[h->t & 1];
+    if (inlet_u) *inlet_u = h->ubc;
+    return STG_OK;
+}
+
+int stg_lbm_info(const stg_lbm *h, stg_info *out)
+{
+    if (!h || !out) return STG_ERR_INVALID;
+    *out = h->info;
+    return STG_OK;
+}
+
+void stg_lbm_destroy(stg_lbm *h) { release(h); }
+
+const char *stg_lbm_last_error(const stg_lbm *h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int stg_mode_draws(uint64_t seed, int32_t n, double *out)
+{
+    if (n < 0 || (n > 0 && !out)) return STG_ERR_INVALID;
+    splitmix_uniform(seed, 4 * n, out);
+    return STG_OK;
+}
+
+const char *stg_lbm_version(void) { return "stglbm 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Kernel argument blocks and launcher declarations shared by the library's
+// translation units (host API, step kernel, inlet kernel).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace stg {
+
+// Step counter on the device.  Step t reads t[t & 1]; the fused step kernel
+// writes t[(t + 1) & 1] = t + 1 when it finishes, so a captured graph can be
+// replayed without host-side parameter updates.
+struct StepCtl {
+    long long t[2];
+    long long t0_filter;  // step at which the temporal filter restarts
+    long long pad;
+};
+
+struct StepArgs {
+    const void *src;      // post-collision populations of the previous step
+    void *dst;            // post-collision populations of this step
+    int nx, ny, nz;
+    unsigned P;           // cells per population plane (nx*ny*nz)
+    int bc_x, bc_y;       // STG_BC_X_*, STG_BC_Y_*
+    float tau0, kq;       // kq = 18 sqrt(2) C  (eq. tau_eff)
+    float Fx, Fy, Fz;
+    int has_force;
+    const float *ubc;     // inlet velocity plane [3][nz][ny]
+    StepCtl *ctl;
+    int parity;
+    int stats_every, check_every;
+    double *stat_mean;    // [3][ny][nx]
+    double *stat_rey;     // [6][ny][nx]
+    double *mass_partial; // [gridDim.x * gridDim.y]
+    unsigned *mass_counter;
+    double *mass_out;     // [0]: last checked mass
+};
+
+struct InletArgs {
+    int ny, nz, N;
+    const float *A;       // [N][ny]  k^n d^n_y (j + 1/2) mod 2 pi
+    const float *B;       // [N][nz]  k^n d^n_z k       mod 2 pi
+    const float *SQ;      // [N][ny]  sqrt(6 q^n(y_j))
+    const float *sig;     // [N][3]   sigma^n
+    const double *phi;    // [N]      phi^n
+    const double *omg;    // [N]      phase advance per step, -2 pi d^n_x U_b / max l_e
+    const float *a6;      // [ny][6]  Cholesky factor a11 a21 a22 a31 a32 a33
+    const float *u_int;   // [ny]     interpolated mean streamwise velocity
+    float a_filter;
+    float *uf;            // [3][nz][ny] filtered fluctuation (state)
+    float *ubc;           // [3][nz][ny] inlet velocity output
+    StepCtl *ctl;
+    int parity;
+};
+
+struct MassArgs {
+    const void *src;
+    unsigned P;
+    int storage;
+    double *partial;
+    unsigned *counter;
+    double *out;
+};
+
+// launchers (return the launch status)
+cudaError_t launch_step(const StepArgs &a, int storage, int collision, cudaStream_t s);
+cudaError_t launch_inlet(const InletArgs &a, cudaStream_t s);
+cudaError_t launch_setup_nodes(int ny, int N, const double *R6, const double *le, const double *leta,
+                               const double *lcut, const double *kn, const double *dk, float *a6,
+                               float *SQ, cudaStream_t s);
+cudaError_t launch_init_equilibrium(void *dst, int storage, int nx, int ny, int nz, const float *u_int,
+                                    cudaStream_t s);
+cudaError_t launch_mass(const MassArgs &a, cudaStream_t s);
+
+int step_grid_blocks(int nx, int ny);
+int mass_grid_blocks();
+
+}  // namespace stg

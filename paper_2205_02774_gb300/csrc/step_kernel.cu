@@ -1,0 +1,412 @@
+// Fused LES-LBM time step for one channel lattice (Algorithm 1, step 12, with
+// steps 9-11 for the inlet nodes and the outlet rebuild folded in).
+//
+// One pass per cell: pull the 19 post-collision populations of the previous
+// step along -c_i (eq. lbe, left side) with half-way bounce-back at the y
+// walls, periodic z (and optionally x, y); rebuild the inlet node (x = 0) by
+// the regularized Zou-He reconstruction (Sec. III.B) and the outlet node
+// (x = nx-1) by the regularized pressure outlet (Sec. IV); take the moments
+// (eqs. density, momentum, tensor); set the Smagorinsky relaxation time
+// (eq. tau_eff); collide (regularized or plain BGK, eqs. lbe, local_eq,
+// bodyforce) and store.  On sampling steps the same pass accumulates the FP64
+// velocity statistics and the FP64 mass.
+//
+// Layout: SoA f[i][z][y][x].  A block is 32 consecutive x (one warp row) by 8
+// z-lanes at one y; each thread walks z with stride 8, so a block owns all z
+// of its (x, y) column and the statistics need no atomics.
+#include <cuda_fp16.h>
+
+#include "d3q19.cuh"
+#include "internal.h"
+
+namespace stg {
+
+constexpr int BX = 32;
+constexpr int BZ = 8;
+
+template <typename S>
+struct Pop;
+
+template <>
+struct Pop<float> {
+    static __device__ __forceinline__ float ld(const float *p, int) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float *p, float v, int) { __stcs(p, v); }
+};
+
+// binary16 storage of f_i - w_i
+template <>
+struct Pop<__half> {
+    static __device__ __forceinline__ float ld(const __half *p, int i) { return w_of(i) + __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half *p, float v, int i) { __stcs(p, __float2half_rn(v - w_of(i))); }
+};
+
+// Regularized rebuild of a boundary node (eqs. f_i, f_i_neq, pi_neq,
+// unknown_neq, bc_eq): the unknown directions (sign(c_x) == SGN) take the
+// non-equilibrium part of their opposite; all 19 are then replaced by
+// f^eq + w_i/(2 cs^4) Q_i : Pi_neq.
+template <int SGN>
+__device__ __forceinline__ void rebuild(float (&f)[Q], float rho, float ux, float uy, float uz)
+{
+    const float uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+        if (cx != SGN) {
+            const float cu = cx * ux + cy * uy + cz * uz;
+            const float feq = w_of(i) * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+            f[i] = f[i] - feq;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        if (cx_of(i) == SGN) f[i] = f[opp_of(i)];
+    float s = 0.f, pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+        const float v = f[i];
+        s += v;
+        if (cx * cx) pxx += v;
+        if (cy * cy) pyy += v;
+        if (cz * cz) pzz += v;
+        if (cx * cy) pxy += cx * cy * v;
+        if (cx * cz) pxz += cx * cz * v;
+        if (cy * cz) pyz += cy * cz * v;
+    }
+    // Pi_neq = sum_i Q_i f_i^neq with Q_i = c_i c_i - I/3
+    pxx -= s * (1.0f / 3.0f);
+    pyy -= s * (1.0f / 3.0f);
+    pzz -= s * (1.0f / 3.0f);
+    const float tr3 = (pxx + pyy + pzz) * (1.0f / 3.0f);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+        const float cu = cx * ux + cy * uy + cz * uz;
+        const float feq = w_of(i) * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+        const float cpc = cx * cx * pxx + cy * cy * pyy + cz * cz * pzz
+                        + 2.0f * (cx * cy * pxy + cx * cz * pxz + cy * cz * pyz);
+        f[i] = feq + 4.5f * w_of(i) * (cpc - tr3);
+    }
+}
+
+template <typename S, bool REG>
+__global__ void __launch_bounds__(BX *BZ, 3) lbm_step_kernel(const StepArgs a)
+{
+    const S *__restrict__ src = static_cast<const S *>(a.src);
+    S *__restrict__ dst = static_cast<S *>(a.dst);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const unsigned P = a.P;
+    const int x = blockIdx.x * BX + threadIdx.x;
+    const int y = blockIdx.y;
+    const int tz = threadIdx.y;
+    const long long t = a.ctl->t[a.parity];
+    const bool do_stats = a.stats_every > 0 && ((t + 1) % a.stats_every) == 0;
+    const bool do_check = a.check_every > 0 && ((t + 1) % a.check_every) == 0;
+    const bool inout = (a.bc_x == 0);
+    const bool walls = (a.bc_y == 0);
+
+    float su0 = 0.f, su1 = 0.f, su2 = 0.f;
+    float s00 = 0.f, s11 = 0.f, s22 = 0.f, s01 = 0.f, s02 = 0.f, s12 = 0.f;
+    float sdr = 0.f;
+
+    if (x < nx) {
+        int xm = x - 1, xp = x + 1;
+        bool xm_ok = true, xp_ok = true;
+        if (inout) {
+            xm_ok = xm >= 0;
+            xp_ok = xp < nx;
+            xm = max(xm, 0);
+            xp = min(xp, nx - 1);
+        } else {
+            if (xm < 0) xm += nx;
+            if (xp >= nx) xp -= nx;
+        }
+        int ym = y - 1, yp = y + 1;
+        bool ym_w = false, yp_w = false;
+        if (walls) {
+            ym_w = ym < 0;
+            yp_w = yp >= ny;
+            ym = max(ym, 0);
+            yp = min(yp, ny - 1);
+        } else {
+            if (ym < 0) ym += ny;
+            if (yp >= ny) yp -= ny;
+        }
+        const float tau0 = a.tau0, kq = a.kq;
+        const float Fx = a.Fx, Fy = a.Fy, Fz = a.Fz;
+        const bool force = a.has_force != 0;
+
+        for (int z = tz; z < nz; z += BZ) {
+            const int zm = (z == 0) ? nz - 1 : z - 1;
+            const int zp = (z == nz - 1) ? 0 : z + 1;
+            const unsigned here = ((unsigned)z * ny + y) * nx + x;
+            float f[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+                const int xs = cx == 0 ? x : (cx > 0 ? xm : xp);
+                const bool xok = cx == 0 ? true : (cx > 0 ? xm_ok : xp_ok);
+                const int ys = cy == 0 ? y : (cy > 0 ? ym : yp);
+                const bool yw = cy == 0 ? false : (cy > 0 ? ym_w : yp_w);
+                const int zs = cz == 0 ? z : (cz > 0 ? zm : zp);
+                const unsigned cell = ((unsigned)zs * ny + ys) * nx + xs;
+                const unsigned pl = yw ? (unsigned)opp_of(i) : (unsigned)i;
+                const unsigned c2 = yw ? here : cell;
+                f[i] = (yw || xok) ? Pop<S>::ld(src + (size_t)pl * P + c2, i) : 0.0f;
+            }
+
+            if (inout && (x == 0 || x == nx - 1)) {
+                if (x == 0) {
+                    const size_t pc = (size_t)z * ny + y, pl3 = (size_t)ny * nz;
+                    const float ubx = a.ubc[pc], uby = a.ubc[pl3 + pc], ubz = a.ubc[2 * pl3 + pc];
+                    // Zou-He density, eq. (density_bc): parallel set + 2 x leaving set
+                    float par = 0.f, lv = 0.f;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        if (cx_of(i) == 0) par += f[i];
+                        if (cx_of(i) < 0) lv += f[i];
+                    }
+                    const float rb = (par + 2.0f * lv) / (1.0f - ubx);
+                    rebuild<1>(f, rb, ubx, uby, ubz);
+                } else {
+                    // zero-gradient velocity from the stored column x = nx-2, rho = 1
+                    const unsigned nb = ((unsigned)z * ny + y) * nx + (nx - 2);
+                    float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        const float v = Pop<S>::ld(src + (size_t)i * P + nb, i);
+                        r += v;
+                        jx += cx_of(i) * v;
+                        jy += cy_of(i) * v;
+                        jz += cz_of(i) * v;
+                    }
+                    const float ir = 1.0f / r;
+                    rebuild<-1>(f, 1.0f, jx * ir, jy * ir, jz * ir);
+                }
+            }
+
+            // moments, eqs. (density), (momentum), (tensor)
+            float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+            float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+                const float v = f[i];
+                rho += v;
+                if (cx) jx += cx * v;
+                if (cy) jy += cy * v;
+                if (cz) jz += cz * v;
+                if (cx) pxx += v;
+                if (cy) pyy += v;
+                if (cz) pzz += v;
+                if (cx * cy) pxy += cx * cy * v;
+                if (cx * cz) pxz += cx * cz * v;
+                if (cy * cz) pyz += cy * cz * v;
+            }
+            const float irho = 1.0f / rho;
+            const float ux = (force ? jx + 0.5f * Fx : jx) * irho;
+            const float uy = (force ? jy + 0.5f * Fy : jy) * irho;
+            const float uz = (force ? jz + 0.5f * Fz : jz) * irho;
+            // Pi_neq = Pi - rho (cs^2 I + u u)
+            const float nxx = pxx - rho * (1.0f / 3.0f + ux * ux);
+            const float nyy = pyy - rho * (1.0f / 3.0f + uy * uy);
+            const float nzz = pzz - rho * (1.0f / 3.0f + uz * uz);
+            const float nxy = pxy - rho * ux * uy;
+            const float nxz = pxz - rho * ux * uz;
+            const float nyz = pyz - rho * uy * uz;
+            const float qh = sqrtf(nxx * nxx + nyy * nyy + nzz * nzz + 2.0f * (nxy * nxy + nxz * nxz + nyz * nyz));
+            // eq. (tau_eff), c = 1: tau = tau0/2 + sqrt((tau0 rho)^2 + 18 sqrt2 C Q^1/2)/(2 rho)
+            const float tau = 0.5f * tau0 + 0.5f * sqrtf(tau0 * tau0 + kq * qh * irho * irho);
+            const float om = 1.0f / tau;
+            const float uu = ux * ux + uy * uy + uz * uz;
+            const float tr3 = (nxx + nyy + nzz) * (1.0f / 3.0f);
+            const float uF = ux * Fx + uy * Fy + uz * Fz;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+                const float w = w_of(i);
+                const float cu = cx * ux + cy * uy + cz * uz;
+                const float feq = w * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+                float fo;
+                if (REG) {
+                    const float cpc = cx * cx * nxx + cy * cy * nyy + cz * cz * nzz
+                                    + 2.0f * (cx * cy * nxy + cx * cz * nxz + cy * cz * nyz);
+                    fo = feq + (1.0f - om) * (4.5f * w * (cpc - tr3));
+                } else {
+                    fo = f[i] - om * (f[i] - feq);
+                }
+                if (force) {
+                    const float cF = cx * Fx + cy * Fy + cz * Fz;
+                    // Guo term, eq. (bodyforce)
+                    fo += (1.0f - 0.5f * om) * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
+                    // regularized: keep the first-order neq part a1 = -F/2
+                    if (REG) fo += (1.0f - om) * (-1.5f * w * cF);
+                }
+                Pop<S>::st(dst + (size_t)i * P + here, fo, i);
+            }
+            if (do_stats) {
+                su0 += ux; su1 += uy; su2 += uz;
+                s00 += ux * ux; s11 += uy * uy; s22 += uz * uz;
+                s01 += ux * uy; s02 += ux * uz; s12 += uy * uz;
+            }
+            if (do_check) sdr += rho - 1.0f;
+        }
+    }
+
+    if (do_stats) {
+        __shared__ float red[9][BZ][BX];
+        const int tx = threadIdx.x;
+        red[0][tz][tx] = su0; red[1][tz][tx] = su1; red[2][tz][tx] = su2;
+        red[3][tz][tx] = s00; red[4][tz][tx] = s11; red[5][tz][tx] = s22;
+        red[6][tz][tx] = s01; red[7][tz][tx] = s02; red[8][tz][tx] = s12;
+        __syncthreads();
+        if (tz == 0 && x < nx) {
+            const size_t xy = (size_t)y * nx + x, m = (size_t)nx * ny;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                double s = 0.0;
+                for (int k = 0; k < BZ; ++k) s += (double)red[q][k][tx];
+                if (q < 3) a.stat_mean[q * m + xy] += s;
+                else a.stat_rey[(q - 3) * m + xy] += s;
+            }
+        }
+    }
+
+    if (do_check) {
+        __shared__ double rd[BZ * BX];
+        __shared__ int s_last;
+        const int tid = threadIdx.y * BX + threadIdx.x;
+        rd[tid] = (double)sdr;
+        __syncthreads();
+        for (int off = BZ * BX / 2; off > 0; off >>= 1) {
+            if (tid < off) rd[tid] += rd[tid + off];
+            __syncthreads();
+        }
+        const unsigned nblocks = gridDim.x * gridDim.y;
+        if (tid == 0) {
+            a.mass_partial[blockIdx.y * gridDim.x + blockIdx.x] = rd[0];
+            __threadfence();
+            const unsigned prev = atomicAdd(a.mass_counter, 1u);
+            s_last = (prev == nblocks - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            double acc = 0.0;
+            for (unsigned k = tid; k < nblocks; k += BZ * BX) acc += __ldcg(a.mass_partial + k);
+            rd[tid] = acc;
+            __syncthreads();
+            for (int off = BZ * BX / 2; off > 0; off >>= 1) {
+                if (tid < off) rd[tid] += rd[tid + off];
+                __syncthreads();
+            }
+            if (tid == 0) {
+                a.mass_out[0] = rd[0] + (double)P;
+                *a.mass_counter = 0u;
+            }
+        }
+    }
+
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+        a.ctl->t[a.parity ^ 1] = t + 1;
+}
+
+int step_grid_blocks(int nx, int ny) { return ((nx + BX - 1) / BX) * ny; }
+
+cudaError_t launch_step(const StepArgs &a, int storage, int collision, cudaStream_t s)
+{
+    dim3 grid((a.nx + BX - 1) / BX, a.ny), block(BX, BZ);
+    if (storage == 0) {
+        if (collision == 0) lbm_step_kernel<float, true><<<grid, block, 0, s>>>(a);
+        else lbm_step_kernel<float, false><<<grid, block, 0, s>>>(a);
+    } else {
+        if (collision == 0) lbm_step_kernel<__half, true><<<grid, block, 0, s>>>(a);
+        else lbm_step_kernel<__half, false><<<grid, block, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Initial state f^eq(1, (u_int(y), 0, 0)) (u_int == nullptr: rest state w_i).
+template <typename S>
+__global__ void init_eq_kernel(S *dst, int nx, int ny, int nz, const float *u_int)
+{
+    const size_t P = (size_t)nx * ny * nz;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < P; c += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)((c / nx) % ny);
+        const float ux = u_int ? u_int[y] : 0.0f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float cu = cx_of(i) * ux;
+            const float feq = w_of(i) * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * ux * ux);
+            Pop<S>::st(dst + (size_t)i * P + c, feq, i);
+        }
+    }
+}
+
+cudaError_t launch_init_equilibrium(void *dst, int storage, int nx, int ny, int nz, const float *u_int, cudaStream_t s)
+{
+    const int blocks = 152 * 8;
+    if (storage == 0) init_eq_kernel<float><<<blocks, 256, 0, s>>>(static_cast<float *>(dst), nx, ny, nz, u_int);
+    else init_eq_kernel<__half><<<blocks, 256, 0, s>>>(static_cast<__half *>(dst), nx, ny, nz, u_int);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 mass of a stored lattice, sum over cells and populations, in a fixed
+// reduction order (block partials, then the last block to finish adds them
+// in index order).
+constexpr int MASS_BLOCKS = 152 * 4;
+constexpr int MASS_THREADS = 256;
+
+template <typename S>
+__global__ void __launch_bounds__(MASS_THREADS) mass_kernel(const MassArgs a)
+{
+    const S *src = static_cast<const S *>(a.src);
+    __shared__ double rd[MASS_THREADS];
+    __shared__ int s_last;
+    double acc = 0.0;
+    for (size_t c = blockIdx.x * (size_t)MASS_THREADS + threadIdx.x; c < a.P; c += (size_t)gridDim.x * MASS_THREADS) {
+        float r = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) r += Pop<S>::ld(src + (size_t)i * a.P + c, i);
+        acc += (double)(r - 1.0f);
+    }
+    const int tid = threadIdx.x;
+    rd[tid] = acc;
+    __syncthreads();
+    for (int off = MASS_THREADS / 2; off > 0; off >>= 1) {
+        if (tid < off) rd[tid] += rd[tid + off];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        a.partial[blockIdx.x] = rd[0];
+        __threadfence();
+        s_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+        double v = 0.0;
+        for (unsigned k = tid; k < gridDim.x; k += MASS_THREADS) v += __ldcg(a.partial + k);
+        rd[tid] = v;
+        __syncthreads();
+        for (int off = MASS_THREADS / 2; off > 0; off >>= 1) {
+            if (tid < off) rd[tid] += rd[tid + off];
+            __syncthreads();
+        }
+        if (tid == 0) {
+            a.out[0] = rd[0] + (double)a.P;
+            *a.counter = 0u;
+        }
+    }
+}
+
+int mass_grid_blocks() { return MASS_BLOCKS; }
+
+cudaError_t launch_mass(const MassArgs &a, cudaStream_t s)
+{
+    if (a.storage == 0) mass_kernel<float><<<MASS_BLOCKS, MASS_THREADS, 0, s>>>(a);
+    else mass_kernel<__half><<<MASS_BLOCKS, MASS_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace stg

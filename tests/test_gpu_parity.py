@@ -1,0 +1,195 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the CPU
+FP64 oracle on identical seeded inputs.
+
+Tolerances (FP32 arithmetic, FP32 or shifted-FP16 storage):
+  * one step from an identical FP32 state: populations, max relative error 1e-5;
+  * inlet velocity plane: max |u_gpu - u_oracle| <= 1e-5 max |u_oracle|;
+  * 200 steps from create() on the 64x32x32 channel: velocity and the
+    accumulated statistics, normwise (max abs error / max abs value) 1e-4;
+  * shifted FP16: one step from an FP16-representable state; each output
+    population within half a binary16 spacing of (f_oracle - w_i) plus 2e-6 |f|.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from workloads import case, perturbed_equilibrium_field
+
+from gpu_helpers import (require_cuda, pair, velocity, max_rel, normwise, fp16_bits, fp16_decode,
+                         fp16_half_ulp, C3)
+
+pytestmark = pytest.mark.gpu
+
+SMALL = case("channel_64x32x32")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    require_cuda()
+
+
+def _single_step(c, seed=1, **kw):
+    gpu, orc = pair(c, **kw)
+    f = perturbed_equilibrium_field(c.nx, c.ny, c.nz, seed=seed).astype(np.float32)
+    gpu.set_state(f, 0)
+    orc.set_pops(f.astype(np.float64))
+    gpu.step(1)
+    orc.step(1)
+    return gpu, orc
+
+
+@pytest.mark.parametrize("collision", ["regularized", "bgk"])
+def test_single_step_channel(collision):
+    c = SMALL.with_(collision=collision, stats_every=0)
+    gpu, orc = _single_step(c)
+    assert max_rel(gpu.populations(), orc.pops()) < 1e-5
+    u_or = orc.inlet()
+    assert np.abs(gpu.inlet() - u_or).max() <= 1e-5 * np.abs(u_or).max()
+
+
+@pytest.mark.parametrize("dims,kw", [
+    ((37, 10, 9), dict()),                                            # ragged x, z; inlet/outlet
+    ((3, 5, 1), dict(n_modes=7)),                                     # smallest inlet/outlet lattice
+    ((33, 7, 11), dict(bc_x="periodic", force=(2e-5, -1e-5, 3e-6))),  # periodic x + walls + force
+    ((16, 12, 10), dict(bc_x="periodic", bc_y="periodic", collision="bgk", force=(1e-5, 0.0, 2e-5))),
+    ((70, 3, 17), dict(collision="bgk", t_filter=0.0)),
+])
+def test_single_step_ragged_and_variants(dims, kw):
+    nx, ny, nz = dims
+    c = SMALL.with_(nx=nx, ny=ny, nz=nz, stats_every=0, **{k: v for k, v in kw.items() if k in
+                                                           ("bc_x", "bc_y", "collision", "force", "n_modes",
+                                                            "t_filter")})
+    gpu, orc = _single_step(c, seed=nx + ny + nz)
+    assert max_rel(gpu.populations(), orc.pops()) < 1e-5
+
+
+def test_inlet_plane_over_time():
+    c = SMALL.with_(stats_every=0, t_filter=4.0)
+    gpu, orc = pair(c)
+    done = 0
+    for n in (1, 2, 7, 40):
+        gpu.step(n - done)
+        orc.step(n - done)
+        done = n
+        u_or = orc.inlet()
+        assert np.abs(gpu.inlet() - u_or).max() <= 1e-5 * np.abs(u_or).max(), n
+
+
+def test_200_steps_channel_velocity_and_statistics():
+    c = SMALL  # 64x32x32, 100 modes, stats every 10 steps, 200 steps
+    gpu, orc = pair(c, check_every=20, mass_tol=0.1)
+    gpu.step(c.steps)
+    orc.step(c.steps)
+    fg, fo = gpu.populations(), orc.pops()
+    assert normwise(velocity(fg), velocity(fo)) < 1e-4
+    st = gpu.stats()
+    assert st["rc"] == 0, st["error"]
+    m, r, n = orc.stats()
+    assert st["n_samples"] == n == c.steps // c.stats_every
+    assert normwise(st["mean_sum"], m) < 1e-4
+    assert normwise(st["rey_sum"], r) < 1e-4
+    # fluctuating part of the Reynolds stress <u'u'> = <uu> - <u><u>
+    cnt = n * c.nz
+    ms, mo = st["mean_sum"] / cnt, m / cnt
+    rs = st["rey_sum"][0] / cnt - ms[0] ** 2
+    ro = r[0] / cnt - mo[0] ** 2
+    assert normwise(rs, ro) < 1e-2
+    assert abs(st["mass"] - fo.sum()) / fo.sum() < 1e-6
+
+
+def test_mass_conservation_periodic_box_gpu():
+    c = SMALL.with_(nx=32, ny=32, nz=32, bc_x="periodic", bc_y="periodic", stats_every=0)
+    from paper_2205_02774_gb300.channel import Channel
+    g = Channel.from_case(c, check_every=100, mass_tol=1e-6)
+    f = perturbed_equilibrium_field(32, 32, 32, seed=9).astype(np.float32)
+    g.set_state(f, 0)
+    m0 = g.stats()["mass0"]
+    g.step(1000)
+    st = g.stats()
+    assert st["rc"] == 0, st["error"]
+    assert abs(st["mass"] / m0 - 1) < 1e-6
+
+
+@pytest.mark.parametrize("collision,lam", [("bgk", lambda t: (t - 0.5) ** 2),
+                                           ("regularized", lambda t: (t - 0.5) * 0.5)])
+def test_poiseuille_gpu(collision, lam):
+    tau, ny = 0.8, 32
+    nu = (tau - 0.5) / 3
+    F = 0.01 * 8 * nu / ny ** 2
+    from paper_2205_02774_gb300.channel import Channel
+    g = Channel(1, ny, 1, tau0=tau, c_smag=0.0, force=(F, 0, 0), bc_x="periodic", bc_y="walls",
+                collision=collision)
+    g.step(int(8 * ny * ny / nu))
+    ux = velocity(g.populations(), (F, 0, 0))[0, 0, :, 0]
+    y = np.arange(ny) + 0.5
+    exact = F / (2 * nu) * (y * (ny - y) + (16 * lam(tau) - 3) / 12)
+    assert normwise(ux, exact) < 2e-4
+
+
+def test_fp16_single_step():
+    c = SMALL.with_(storage="fp16s", stats_every=0)
+    gpu, orc = pair(c)
+    f = perturbed_equilibrium_field(c.nx, c.ny, c.nz, seed=4)
+    bits = fp16_bits(f)
+    gpu.set_state(bits, 0)
+    orc.set_pops(fp16_decode(bits))
+    gpu.step(1)
+    orc.step(1)
+    fo = orc.pops()
+    fg = fp16_decode(gpu.get_state())
+    W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12).reshape(19, 1, 1, 1)
+    bound = fp16_half_ulp(fo - W) + 2e-6 * np.abs(fo)
+    excess = np.abs(fg - fo) - bound
+    assert excess.max() <= 0, float(excess.max())
+
+
+def _boundary_samples(nx, ny, nz, rng, n_random=1500):
+    pts = set()
+    for x in (0, 1, nx - 2, nx - 1):
+        for y in (0, 1, ny // 2, ny - 2, ny - 1):
+            for z in (0, nz // 3, nz - 1):
+                pts.add((x, y, z))
+    xs = rng.integers(0, nx, n_random)
+    ys = rng.integers(0, ny, n_random)
+    zs = rng.integers(0, nz, n_random)
+    pts.update(zip(xs.tolist(), ys.tolist(), zs.tolist()))
+    return sorted(pts)
+
+
+@pytest.mark.parametrize("name,storage", [("channel_768x128x192", "fp32"), ("channel_768x128x192", "fp16s")])
+def test_full_size_sampled_cells(name, storage):
+    """Full-size lattice in the benchmark's launch configuration: one step from
+    the GPU's own state after a few steps, checked cell by cell by the oracle
+    on ~1500 random cells plus every boundary class; the whole inlet plane is
+    checked against the oracle's generator over the same steps."""
+    import oracle as O
+    c = case(name).with_(storage=storage)
+    gpu, orc = pair(c, check_every=10, mass_tol=0.1, oracle_nx=3)
+    gpu.step(3)
+    orc.step(4)  # the small oracle lattice only supplies the inlet planes
+    pre = gpu.get_state()
+    gpu.step(1)
+    post = gpu.get_state()
+    u_or = orc.inlet()
+    u_g = gpu.inlet()
+    assert np.abs(u_g - u_or).max() <= 1e-5 * np.abs(u_or).max()
+    dom = O.make_domain(c.nx, c.ny, c.nz, c.tau0, c.c_smag, c.force, c.bc_x, c.bc_y, c.collision)
+    rng = np.random.default_rng(2024)
+    W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    worst = 0.0
+    for (x, y, z) in _boundary_samples(c.nx, c.ny, c.nz, rng):
+        ref = O.cell_update(dom, pre, x, y, z, u_or[:, z, y])
+        if storage == "fp32":
+            got = post[:, z, y, x].astype(np.float64)
+            worst = max(worst, float(np.max(np.abs(got - ref) / np.abs(ref))))
+        else:
+            got = post[:, z, y, x].view(np.float16).astype(np.float64) + W
+            bound = fp16_half_ulp(ref - W) + 2e-6 * np.abs(ref)
+            worst = max(worst, float(np.max(np.abs(got - ref) - bound)))
+    if storage == "fp32":
+        assert worst < 1e-5
+    else:
+        assert worst <= 0
+    st = gpu.stats()
+    assert st["rc"] == 0 and math.isfinite(st["mass"])
