@@ -22,8 +22,9 @@
  *       6:(0,0,-1) 7:(1,1,0)  8:(-1,-1,0) 9:(1,-1,0) 10:(-1,1,0) 11:(1,0,1)
  *       12:(-1,0,-1) 13:(1,0,-1) 14:(-1,0,1) 15:(0,1,1) 16:(0,-1,-1)
  *       17:(0,1,-1) 18:(0,-1,1)
- *   - Population layout f[i][z][y][x], x fastest.  STG_FP32 stores f_i as
- *     float; STG_FP16_SHIFTED stores f_i - w_i as IEEE binary16.
+ *   - Population layout f[i][z][y][x], x fastest.  Both storage formats hold
+ *     the shifted population g_i = f_i - w_i (w_i the D3Q19 weight): as float
+ *     for STG_FP32, as IEEE binary16 for STG_FP16_SHIFTED.
  *   - Populations held by a handle between steps are post-collision.
  *   - Inlet plane layout u[c][z][y] (y fastest), lattice units.
  *   - Statistics layout s[k][y][x] (x fastest).
@@ -172,7 +173,8 @@ int stg_lbm_step_timed(stg_lbm *h, int64_t n, double *ms_step, double *ms_inlet)
  * wait expires, STG_ERR_UNSTABLE if a check failed. */
 int stg_lbm_stats(stg_lbm *h, stg_stats *out);
 
-/* Copy the populations (storage format, 19*nx*ny*nz elements of 4 or 2 bytes)
+/* Copy the populations (storage format g_i = f_i - w_i, 19*nx*ny*nz elements
+ * of 4 or 2 bytes)
  * to or from host memory.  set_state also sets the step counter to `step` and
  * restarts the temporal filter.  `bytes` must equal the state size. */
 int stg_lbm_get_state(stg_lbm *h, void *host, size_t bytes);

@@ -228,14 +228,15 @@ def unit_scales(prof, tau0, ny, mach_target):
     return cx[0], ct[0]
 
 
-def cell_update(domain, src, x, y, z, u_bc=(0.0, 0.0, 0.0)):
+def cell_update(domain, src, x, y, z, u_bc=(0.0, 0.0, 0.0), shifted=False):
     """One cell's post-step populations from a stored lattice.
 
-    ``src`` is float64, float32, or uint16 (binary16 bits of f_i - w_i)."""
+    ``src`` is float64 (f), float32 (f, or f_i - w_i with ``shifted``), or
+    uint16 (binary16 bits of f_i - w_i)."""
     if src.dtype == np.float64:
         t = 0
     elif src.dtype == np.float32:
-        t = 1
+        t = 3 if shifted else 1
     elif src.dtype == np.uint16:
         t = 2
     else:

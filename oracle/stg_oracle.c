@@ -354,6 +354,7 @@ static double load(int32_t type, const void *src, size_t ncell, int i, size_t ce
     size_t idx = (size_t)i * ncell + cell;
     if (type == 0) return ((const double *)src)[idx];
     if (type == 1) return (double)((const float *)src)[idx];
+    if (type == 3) return weight(i) + (double)((const float *)src)[idx];
     return weight(i) + orc_f16_to_double(((const uint16_t *)src)[idx]);
 }
 

@@ -67,8 +67,9 @@ void   orc_filter_update(int32_t first, double a, const double *u_raw, double *u
 double orc_f16_to_double(uint16_t h);
 
 /* ---- one cell of one step, read from an arbitrary stored lattice ----
- * src_type 0: double f[19][nz][ny][nx]; 1: float; 2: binary16 bits of
- * (f_i - w_i).  u_bc3 is the inlet velocity of node (y,z) (used at x=0).   */
+ * src_type 0: double f[19][nz][ny][nx]; 1: float f; 2: binary16 bits of
+ * (f_i - w_i); 3: float (f_i - w_i).  u_bc3 is the inlet velocity of node
+ * (y,z) (used at x=0).                                                      */
 void orc_cell_update(const orc_domain *d, int32_t src_type, const void *src,
                      int32_t x, int32_t y, int32_t z, const double *u_bc3, double *out19);
 

@@ -12,6 +12,9 @@ import numpy as np
 
 from . import capi as A
 
+# D3Q19 weights of the documented population order (rest, axis, edge)
+W19 = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
 
 class _TorchAllocator:
     """stg_allocator backed by torch.cuda.caching_allocator_alloc/delete."""
@@ -124,13 +127,21 @@ class Channel:
         assert arr.shape == self.shape
         A.stg_lbm_set_state(self.h, arr, step)
 
+    def encode(self, f):
+        """Storage format (g_i = f_i - w_i as float32 or binary16 bits) of populations f."""
+        g = np.asarray(f, dtype=np.float64) - W19[:, None, None, None]
+        if self.storage == "fp32":
+            return np.ascontiguousarray(g.astype(np.float32))
+        return np.ascontiguousarray(g.astype(np.float16).view(np.uint16))
+
+    def decode(self, s):
+        """float64 populations f_i from the storage format."""
+        g = s.astype(np.float64) if self.storage == "fp32" else s.view(np.float16).astype(np.float64)
+        return g + W19[:, None, None, None]
+
     def populations(self):
         """Current populations as float64 f_i (decoded from the storage format)."""
-        s = self.get_state()
-        if self.storage == "fp32":
-            return s.astype(np.float64)
-        w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12, dtype=np.float32)
-        return (s.view(np.float16).astype(np.float32) + w[:, None, None, None]).astype(np.float64)
+        return self.decode(self.get_state())
 
     def inlet(self):
         out = np.empty((3, self.nz, self.ny), dtype=np.float32)

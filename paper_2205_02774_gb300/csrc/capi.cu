@@ -415,6 +415,7 @@ int reset_counters(stg_lbm *h, int64_t step)
     const size_t m = (size_t)h->d.nx * h->d.ny;
     CK(cudaMemsetAsync(h->stat_mean, 0, sizeof(double) * 3 * m, h->stream));
     CK(cudaMemsetAsync(h->stat_rey, 0, sizeof(double) * 6 * m, h->stream));
+    CK(cudaMemsetAsync(h->mass_out, 0, sizeof(double) * 2, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->t = step;
     h->t0_stats = step;
@@ -599,7 +600,8 @@ int stg_lbm_step(stg_lbm *h, int64_t n)
         h->t += k;
         n -= k;
     }
-    if (h->d.check_every > 0) {
+    // read back the last check only once a check step has run since the reset
+    if (h->d.check_every > 0 && h->t / h->d.check_every > h->t0_stats / h->d.check_every) {
         CK(cudaMemcpyAsync(h->h_pinned, h->mass_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaEventRecord(h->ev_check, h->stream));
         h->check_pending = true;

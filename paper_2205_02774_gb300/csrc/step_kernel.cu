@@ -24,47 +24,53 @@ namespace stg {
 constexpr int BX = 32;
 constexpr int BZ = 8;
 
+// Both storage formats hold the shifted population g_i = f_i - w_i, and all
+// arithmetic below works on g: the rest weights never enter a sum, so FP32
+// rounding acts on the small fluctuating part only (no weight-rounding bias
+// in the mass, no loss of the low-order bits of slow flows).
 template <typename S>
 struct Pop;
 
 template <>
 struct Pop<float> {
-    static __device__ __forceinline__ float ld(const float *p, int) { return __ldg(p); }
-    static __device__ __forceinline__ void st(float *p, float v, int) { __stcs(p, v); }
+    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float *p, float g) { __stcs(p, g); }
 };
 
-// binary16 storage of f_i - w_i
 template <>
 struct Pop<__half> {
-    static __device__ __forceinline__ float ld(const __half *p, int i) { return w_of(i) + __half2float(__ldg(p)); }
-    static __device__ __forceinline__ void st(__half *p, float v, int i) { __stcs(p, __float2half_rn(v - w_of(i))); }
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half *p, float g) { __stcs(p, __float2half_rn(g)); }
 };
+
+// shifted equilibrium g^eq_i = f^eq_i - w_i = w_i [drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)]
+__device__ __forceinline__ float geq(float w, float drho, float rho, float cu, float uu)
+{
+    return w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+}
 
 // Regularized rebuild of a boundary node (eqs. f_i, f_i_neq, pi_neq,
 // unknown_neq, bc_eq): the unknown directions (sign(c_x) == SGN) take the
 // non-equilibrium part of their opposite; all 19 are then replaced by
 // f^eq + w_i/(2 cs^4) Q_i : Pi_neq.
 template <int SGN>
-__device__ __forceinline__ void rebuild(float (&f)[Q], float rho, float ux, float uy, float uz)
+__device__ __forceinline__ void rebuild(float (&g)[Q], float drho, float ux, float uy, float uz)
 {
+    const float rho = 1.0f + drho;
     const float uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        if (cx != SGN) {
-            const float cu = cx * ux + cy * uy + cz * uz;
-            const float feq = w_of(i) * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
-            f[i] = f[i] - feq;
-        }
+        if (cx != SGN) g[i] = g[i] - geq(w_of(i), drho, rho, cx * ux + cy * uy + cz * uz, uu);
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-        if (cx_of(i) == SGN) f[i] = f[opp_of(i)];
+        if (cx_of(i) == SGN) g[i] = g[opp_of(i)];
     float s = 0.f, pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const float v = f[i];
+        const float v = g[i];
         s += v;
         if (cx * cx) pxx += v;
         if (cy * cy) pyy += v;
@@ -81,11 +87,9 @@ __device__ __forceinline__ void rebuild(float (&f)[Q], float rho, float ux, floa
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const float cu = cx * ux + cy * uy + cz * uz;
-        const float feq = w_of(i) * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
         const float cpc = cx * cx * pxx + cy * cy * pyy + cz * cz * pzz
                         + 2.0f * (cx * cy * pxy + cx * cz * pxz + cy * cz * pyz);
-        f[i] = feq + 4.5f * w_of(i) * (cpc - tr3);
+        g[i] = geq(w_of(i), drho, rho, cx * ux + cy * uy + cz * uz, uu) + 4.5f * w_of(i) * (cpc - tr3);
     }
 }
 
@@ -152,47 +156,50 @@ __global__ void __launch_bounds__(BX *BZ, 3) lbm_step_kernel(const StepArgs a)
                 const unsigned cell = ((unsigned)zs * ny + ys) * nx + xs;
                 const unsigned pl = yw ? (unsigned)opp_of(i) : (unsigned)i;
                 const unsigned c2 = yw ? here : cell;
-                f[i] = (yw || xok) ? Pop<S>::ld(src + (size_t)pl * P + c2, i) : 0.0f;
+                f[i] = (yw || xok) ? Pop<S>::ld(src + (size_t)pl * P + c2) : 0.0f;
             }
 
             if (inout && (x == 0 || x == nx - 1)) {
                 if (x == 0) {
                     const size_t pc = (size_t)z * ny + y, pl3 = (size_t)ny * nz;
                     const float ubx = a.ubc[pc], uby = a.ubc[pl3 + pc], ubz = a.ubc[2 * pl3 + pc];
-                    // Zou-He density, eq. (density_bc): parallel set + 2 x leaving set
+                    // Zou-He density, eq. (density_bc): parallel set + 2 x leaving set.
+                    // The weights of that combination sum to 1 (2/3 + 2 x 1/6), so
+                    // rho_bc - 1 = (S_g + u_x)/(1 - u_x) with S_g the same sum of g.
                     float par = 0.f, lv = 0.f;
 #pragma unroll
                     for (int i = 0; i < Q; ++i) {
                         if (cx_of(i) == 0) par += f[i];
                         if (cx_of(i) < 0) lv += f[i];
                     }
-                    const float rb = (par + 2.0f * lv) / (1.0f - ubx);
-                    rebuild<1>(f, rb, ubx, uby, ubz);
+                    const float drb = (par + 2.0f * lv + ubx) / (1.0f - ubx);
+                    rebuild<1>(f, drb, ubx, uby, ubz);
                 } else {
                     // zero-gradient velocity from the stored column x = nx-2, rho = 1
                     const unsigned nb = ((unsigned)z * ny + y) * nx + (nx - 2);
                     float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
                     for (int i = 0; i < Q; ++i) {
-                        const float v = Pop<S>::ld(src + (size_t)i * P + nb, i);
+                        const float v = Pop<S>::ld(src + (size_t)i * P + nb);
                         r += v;
                         jx += cx_of(i) * v;
                         jy += cy_of(i) * v;
                         jz += cz_of(i) * v;
                     }
-                    const float ir = 1.0f / r;
-                    rebuild<-1>(f, 1.0f, jx * ir, jy * ir, jz * ir);
+                    const float ir = 1.0f / (1.0f + r);
+                    rebuild<-1>(f, 0.0f, jx * ir, jy * ir, jz * ir);
                 }
             }
 
-            // moments, eqs. (density), (momentum), (tensor)
-            float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+            // moments, eqs. (density), (momentum), (tensor), on g = f - w:
+            // rho = 1 + sum g, rho u = sum c g (+ F/2), Pi = sum c c g + I/3
+            float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
             float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
                 const float v = f[i];
-                rho += v;
+                drho += v;
                 if (cx) jx += cx * v;
                 if (cy) jy += cy * v;
                 if (cz) jz += cz * v;
@@ -203,14 +210,15 @@ __global__ void __launch_bounds__(BX *BZ, 3) lbm_step_kernel(const StepArgs a)
                 if (cx * cz) pxz += cx * cz * v;
                 if (cy * cz) pyz += cy * cz * v;
             }
+            const float rho = 1.0f + drho;
             const float irho = 1.0f / rho;
             const float ux = (force ? jx + 0.5f * Fx : jx) * irho;
             const float uy = (force ? jy + 0.5f * Fy : jy) * irho;
             const float uz = (force ? jz + 0.5f * Fz : jz) * irho;
-            // Pi_neq = Pi - rho (cs^2 I + u u)
-            const float nxx = pxx - rho * (1.0f / 3.0f + ux * ux);
-            const float nyy = pyy - rho * (1.0f / 3.0f + uy * uy);
-            const float nzz = pzz - rho * (1.0f / 3.0f + uz * uz);
+            // Pi_neq = Pi - rho (cs^2 I + u u) = sum c c g - drho/3 I - rho u u
+            const float nxx = pxx - drho * (1.0f / 3.0f) - rho * ux * ux;
+            const float nyy = pyy - drho * (1.0f / 3.0f) - rho * uy * uy;
+            const float nzz = pzz - drho * (1.0f / 3.0f) - rho * uz * uz;
             const float nxy = pxy - rho * ux * uy;
             const float nxz = pxz - rho * ux * uz;
             const float nyz = pyz - rho * uy * uz;
@@ -226,30 +234,30 @@ __global__ void __launch_bounds__(BX *BZ, 3) lbm_step_kernel(const StepArgs a)
                 const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
                 const float w = w_of(i);
                 const float cu = cx * ux + cy * uy + cz * uz;
-                const float feq = w * rho * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
-                float fo;
+                const float ge = geq(w, drho, rho, cu, uu);
+                float go;
                 if (REG) {
                     const float cpc = cx * cx * nxx + cy * cy * nyy + cz * cz * nzz
                                     + 2.0f * (cx * cy * nxy + cx * cz * nxz + cy * cz * nyz);
-                    fo = feq + (1.0f - om) * (4.5f * w * (cpc - tr3));
+                    go = ge + (1.0f - om) * (4.5f * w * (cpc - tr3));
                 } else {
-                    fo = f[i] - om * (f[i] - feq);
+                    go = f[i] - om * (f[i] - ge);
                 }
                 if (force) {
                     const float cF = cx * Fx + cy * Fy + cz * Fz;
                     // Guo term, eq. (bodyforce)
-                    fo += (1.0f - 0.5f * om) * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
+                    go += (1.0f - 0.5f * om) * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
                     // regularized: keep the first-order neq part a1 = -F/2
-                    if (REG) fo += (1.0f - om) * (-1.5f * w * cF);
+                    if (REG) go += (1.0f - om) * (-1.5f * w * cF);
                 }
-                Pop<S>::st(dst + (size_t)i * P + here, fo, i);
+                Pop<S>::st(dst + (size_t)i * P + here, go);
             }
             if (do_stats) {
                 su0 += ux; su1 += uy; su2 += uz;
                 s00 += ux * ux; s11 += uy * uy; s22 += uz * uz;
                 s01 += ux * uy; s02 += ux * uz; s12 += uy * uz;
             }
-            if (do_check) sdr += rho - 1.0f;
+            if (do_check) sdr += drho;
         }
     }
 
@@ -326,7 +334,8 @@ cudaError_t launch_step(const StepArgs &a, int storage, int collision, cudaStrea
 }
 
 // ---------------------------------------------------------------------------
-// Initial state f^eq(1, (u_int(y), 0, 0)) (u_int == nullptr: rest state w_i).
+// Initial state f^eq(1, (u_int(y), 0, 0)) (u_int == nullptr: rest state),
+// stored shifted.
 template <typename S>
 __global__ void init_eq_kernel(S *dst, int nx, int ny, int nz, const float *u_int)
 {
@@ -335,11 +344,7 @@ __global__ void init_eq_kernel(S *dst, int nx, int ny, int nz, const float *u_in
         const int y = (int)((c / nx) % ny);
         const float ux = u_int ? u_int[y] : 0.0f;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float cu = cx_of(i) * ux;
-            const float feq = w_of(i) * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * ux * ux);
-            Pop<S>::st(dst + (size_t)i * P + c, feq, i);
-        }
+        for (int i = 0; i < Q; ++i) Pop<S>::st(dst + (size_t)i * P + c, geq(w_of(i), 0.0f, 1.0f, cx_of(i) * ux, ux * ux));
     }
 }
 
@@ -368,8 +373,8 @@ __global__ void __launch_bounds__(MASS_THREADS) mass_kernel(const MassArgs a)
     for (size_t c = blockIdx.x * (size_t)MASS_THREADS + threadIdx.x; c < a.P; c += (size_t)gridDim.x * MASS_THREADS) {
         float r = 0.f;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) r += Pop<S>::ld(src + (size_t)i * a.P + c, i);
-        acc += (double)(r - 1.0f);
+        for (int i = 0; i < Q; ++i) r += Pop<S>::ld(src + (size_t)i * a.P + c);
+        acc += (double)r;
     }
     const int tid = threadIdx.x;
     rd[tid] = acc;

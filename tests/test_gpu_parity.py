@@ -31,9 +31,9 @@ def _cuda():
 
 def _single_step(c, seed=1, **kw):
     gpu, orc = pair(c, **kw)
-    f = perturbed_equilibrium_field(c.nx, c.ny, c.nz, seed=seed).astype(np.float32)
-    gpu.set_state(f, 0)
-    orc.set_pops(f.astype(np.float64))
+    st = gpu.encode(perturbed_equilibrium_field(c.nx, c.ny, c.nz, seed=seed))
+    gpu.set_state(st, 0)
+    orc.set_pops(gpu.decode(st))
     gpu.step(1)
     orc.step(1)
     return gpu, orc
@@ -102,8 +102,7 @@ def test_mass_conservation_periodic_box_gpu():
     c = SMALL.with_(nx=32, ny=32, nz=32, bc_x="periodic", bc_y="periodic", stats_every=0)
     from paper_2205_02774_gb300.channel import Channel
     g = Channel.from_case(c, check_every=100, mass_tol=1e-6)
-    f = perturbed_equilibrium_field(32, 32, 32, seed=9).astype(np.float32)
-    g.set_state(f, 0)
+    g.set_state(g.encode(perturbed_equilibrium_field(32, 32, 32, seed=9)), 0)
     m0 = g.stats()["mass0"]
     g.step(1000)
     st = g.stats()
@@ -179,9 +178,9 @@ def test_full_size_sampled_cells(name, storage):
     W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
     worst = 0.0
     for (x, y, z) in _boundary_samples(c.nx, c.ny, c.nz, rng):
-        ref = O.cell_update(dom, pre, x, y, z, u_or[:, z, y])
+        ref = O.cell_update(dom, pre, x, y, z, u_or[:, z, y], shifted=True)
         if storage == "fp32":
-            got = post[:, z, y, x].astype(np.float64)
+            got = post[:, z, y, x].astype(np.float64) + W
             worst = max(worst, float(np.max(np.abs(got - ref) / np.abs(ref))))
         else:
             got = post[:, z, y, x].view(np.float16).astype(np.float64) + W

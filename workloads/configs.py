@@ -56,6 +56,8 @@ CASES = {
     # production FP32 channel: h = 64, 12h x 2h x 3h, 200 modes, 96 FV cells
     "channel_768x128x192": ChannelCase("channel_768x128x192", 768, 128, 192,
                                        n_modes=200, n_fv=96, steps=20000),
+    # mid-size channel (h = 32) used for detailed profiles: 2.4M cells, lattice > L2
+    "channel_384x64x96": ChannelCase("channel_384x64x96", 384, 64, 96, n_modes=200, n_fv=96, steps=2000),
     # refined channel: h = 128, 151M cells
     "channel_1536x256x384": ChannelCase("channel_1536x256x384", 1536, 256, 384,
                                         n_modes=200, n_fv=96, steps=20000),
