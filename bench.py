@@ -261,12 +261,13 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (lattice %.2f GB)" % (2 * 19 * c.cells * bpc / 38 / 1e9),
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "lbm_step_kernel", "kernel_ms": ms_step,
+                     "traffic": traffic, "kernel": "lbm_step_kernel + lbm_edge_kernel (one fused step pass)",
+                     "kernel_ms": ms_step,
                      "bytes_per_cell": bpc, "peak_source": f"{peak_kind} hbm_gbs (copy)",
                      "inlet_kernel_ms": ms_inlet},
         "hbm_frac_of_step": bpc * c.cells * args.steps / (ms * 1e-3) / 1e9 / peak,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 3 * args.steps,  # inlet + interior step + edge step kernels per step
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

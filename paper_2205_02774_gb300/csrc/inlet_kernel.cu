@@ -9,23 +9,28 @@
 //   u_bc = u_int(j) e_x + u_f                                               eqs. (u_phys), (u_transfer)
 // The phase is split into three parts each already reduced to [0, 2 pi):
 // the y part and the z part (tables built in FP64 on the host) and the time
-// part phi^n + omega^n t (evaluated in FP64 per block), so the FP32 cosine
-// sees an argument below 6 pi whatever the step count.
+// part phi^n + omega^n t (evaluated in FP64 per block); their FP32 sum is
+// below 6 pi whatever the step count and is reduced to [-pi, pi] before the
+// cosine.  Each block serves 32 nodes; its 8 warps split the mode sum.
 #include "internal.h"
 
 namespace stg {
 
-constexpr int INLET_THREADS = 128;
+constexpr int INLET_NODES = 32;  // nodes per block (one per lane)
+constexpr int INLET_WARPS = 8;   // the mode sum of each node is split over 8 warps
 constexpr double TWO_PI = 6.283185307179586476925286766559;
 
-__global__ void __launch_bounds__(INLET_THREADS) stg_inlet_kernel(const InletArgs a)
+__global__ void __launch_bounds__(INLET_NODES *INLET_WARPS) stg_inlet_kernel(const InletArgs a)
 {
     extern __shared__ float sm[];  // theta[N], sigma[3N]
+    __shared__ float part[INLET_WARPS][3][INLET_NODES];
     float *theta = sm;
     float *sig = sm + a.N;
+    const int tid = threadIdx.y * INLET_NODES + threadIdx.x;
     const long long t = a.ctl->t[a.parity];
     const bool first = (t == a.ctl->t0_filter);
-    for (int n = threadIdx.x; n < a.N; n += blockDim.x) {
+    // time part of the phase, phi^n + omega^n t, reduced to [0, 2 pi) in FP64
+    for (int n = tid; n < a.N; n += INLET_NODES * INLET_WARPS) {
         double th = a.phi[n] + a.omg[n] * (double)t;
         th -= TWO_PI * floor(th / TWO_PI);
         theta[n] = (float)th;
@@ -34,17 +39,32 @@ __global__ void __launch_bounds__(INLET_THREADS) stg_inlet_kernel(const InletArg
         sig[3 * n + 2] = a.sig[3 * n + 2];
     }
     __syncthreads();
-    const int node = blockIdx.x * blockDim.x + threadIdx.x;
     const int ny = a.ny, nz = a.nz;
-    if (node >= ny * nz) return;
-    const int j = node % ny, k = node / ny;
+    const int node = blockIdx.x * INLET_NODES + threadIdx.x;
+    const bool live = node < ny * nz;
+    const int j = live ? node % ny : 0, k = live ? node / ny : 0;
     float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-    for (int n = 0; n < a.N; ++n) {
-        const float arg = a.A[(size_t)n * ny + j] + a.B[(size_t)n * nz + k] + theta[n];
-        const float amp = a.SQ[(size_t)n * ny + j] * cosf(arg);
-        v0 = fmaf(amp, sig[3 * n + 0], v0);
-        v1 = fmaf(amp, sig[3 * n + 1], v1);
-        v2 = fmaf(amp, sig[3 * n + 2], v2);
+    if (live) {
+        for (int n = threadIdx.y; n < a.N; n += INLET_WARPS) {
+            float arg = a.A[(size_t)n * ny + j] + a.B[(size_t)n * nz + k] + theta[n];  // in [0, 6 pi)
+            arg -= 6.2831853f * rintf(arg * 0.15915494f);                             // to [-pi, pi]
+            const float amp = a.SQ[(size_t)n * ny + j] * __cosf(arg);
+            v0 = fmaf(amp, sig[3 * n + 0], v0);
+            v1 = fmaf(amp, sig[3 * n + 1], v1);
+            v2 = fmaf(amp, sig[3 * n + 2], v2);
+        }
+    }
+    part[threadIdx.y][0][threadIdx.x] = v0;
+    part[threadIdx.y][1][threadIdx.x] = v1;
+    part[threadIdx.y][2][threadIdx.x] = v2;
+    __syncthreads();
+    if (threadIdx.y != 0 || !live) return;
+    v0 = v1 = v2 = 0.f;
+#pragma unroll
+    for (int w = 0; w < INLET_WARPS; ++w) {
+        v0 += part[w][0][threadIdx.x];
+        v1 += part[w][1][threadIdx.x];
+        v2 += part[w][2][threadIdx.x];
     }
     const float *L = a.a6 + 6 * j;
     const float u0 = L[0] * v0;
@@ -69,9 +89,9 @@ __global__ void __launch_bounds__(INLET_THREADS) stg_inlet_kernel(const InletArg
 cudaError_t launch_inlet(const InletArgs &a, cudaStream_t s)
 {
     const int nodes = a.ny * a.nz;
-    const int blocks = (nodes + INLET_THREADS - 1) / INLET_THREADS;
+    const int blocks = (nodes + INLET_NODES - 1) / INLET_NODES;
     const size_t smem = sizeof(float) * 4 * (size_t)(a.N > 0 ? a.N : 1);
-    stg_inlet_kernel<<<blocks, INLET_THREADS, smem, s>>>(a);
+    stg_inlet_kernel<<<blocks, dim3(INLET_NODES, INLET_WARPS), smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -100,25 +120,41 @@ __device__ double vk_spectrum(double k, double le, double leta, double lcut)
     return e;
 }
 
-__global__ void setup_nodes_kernel(int ny, int N, const double *R6, const double *le, const double *leta,
-                                   const double *lcut, const double *kn, const double *dk, float *a6, float *SQ)
+// One block per inlet node j; its threads share the mode sum (FP64, fixed
+// reduction order).
+constexpr int SETUP_THREADS = 128;
+
+__global__ void __launch_bounds__(SETUP_THREADS) setup_nodes_kernel(int ny, int N, const double *R6, const double *le,
+                                                                     const double *leta, const double *lcut,
+                                                                     const double *kn, const double *dk, float *a6,
+                                                                     float *SQ)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= ny) return;
-    const double *R = R6 + 6 * j;  // 11 22 33 12 13 23
-    const double l11 = sqrt(fmax(R[0], 0.0));
-    const double l21 = l11 > 0.0 ? R[3] / l11 : 0.0;
-    const double l31 = l11 > 0.0 ? R[4] / l11 : 0.0;
-    const double l22 = sqrt(fmax(R[1] - l21 * l21, 0.0));
-    const double l32 = l22 > 0.0 ? (R[5] - l21 * l31) / l22 : 0.0;
-    const double l33 = sqrt(fmax(R[2] - l31 * l31 - l32 * l32, 0.0));
-    float *o = a6 + 6 * j;
-    o[0] = (float)l11; o[1] = (float)l21; o[2] = (float)l22;
-    o[3] = (float)l31; o[4] = (float)l32; o[5] = (float)l33;
-    double total = 0.0;
-    for (int n = 0; n < N; ++n) total += vk_spectrum(kn[n], le[j], leta[j], lcut[j]) * dk[n];
-    for (int n = 0; n < N; ++n) {
-        const double q = total > 0.0 ? vk_spectrum(kn[n], le[j], leta[j], lcut[j]) * dk[n] / total : 0.0;
+    __shared__ double red[SETUP_THREADS];
+    const int j = blockIdx.x;
+    if (threadIdx.x == 0) {
+        const double *R = R6 + 6 * j;  // 11 22 33 12 13 23
+        const double l11 = sqrt(fmax(R[0], 0.0));
+        const double l21 = l11 > 0.0 ? R[3] / l11 : 0.0;
+        const double l31 = l11 > 0.0 ? R[4] / l11 : 0.0;
+        const double l22 = sqrt(fmax(R[1] - l21 * l21, 0.0));
+        const double l32 = l22 > 0.0 ? (R[5] - l21 * l31) / l22 : 0.0;
+        const double l33 = sqrt(fmax(R[2] - l31 * l31 - l32 * l32, 0.0));
+        float *o = a6 + 6 * j;
+        o[0] = (float)l11; o[1] = (float)l21; o[2] = (float)l22;
+        o[3] = (float)l31; o[4] = (float)l32; o[5] = (float)l33;
+    }
+    const double lej = le[j], letaj = leta[j], lcutj = lcut[j];
+    double acc = 0.0;
+    for (int n = threadIdx.x; n < N; n += SETUP_THREADS) acc += vk_spectrum(kn[n], lej, letaj, lcutj) * dk[n];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = SETUP_THREADS / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    const double total = red[0];
+    for (int n = threadIdx.x; n < N; n += SETUP_THREADS) {
+        const double q = total > 0.0 ? vk_spectrum(kn[n], lej, letaj, lcutj) * dk[n] / total : 0.0;
         SQ[(size_t)n * ny + j] = (float)sqrt(6.0 * q);
     }
 }
@@ -127,7 +163,7 @@ cudaError_t launch_setup_nodes(int ny, int N, const double *R6, const double *le
                                const double *lcut, const double *kn, const double *dk, float *a6, float *SQ,
                                cudaStream_t s)
 {
-    setup_nodes_kernel<<<(ny + 63) / 64, 64, 0, s>>>(ny, N, R6, le, leta, lcut, kn, dk, a6, SQ);
+    setup_nodes_kernel<<<ny, SETUP_THREADS, 0, s>>>(ny, N, R6, le, leta, lcut, kn, dk, a6, SQ);
     return cudaGetLastError();
 }
 
