@@ -11,6 +11,7 @@
 #include <utility>
 #include <vector>
 
+#include "d3q19.cuh"
 #include "internal.h"
 #include "stg_lbm.h"
 
@@ -49,6 +50,8 @@ struct stg_lbm {
     unsigned *m_counter = nullptr;
     double *h_pinned = nullptr;  // [0]: last checked mass
     cudaEvent_t ev_check = nullptr, ev_done = nullptr;
+    cudaStream_t side = nullptr;                       // branch for the edge kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool check_pending = false;
     int64_t t = 0, t0_stats = 0;
     double mass0 = 0.0;
@@ -280,6 +283,14 @@ stg::StepArgs step_args(const stg_lbm *h, int parity)
     stg::StepArgs a{};
     a.src = h->lat[parity];
     a.dst = h->lat[parity ^ 1];
+    for (int i = 0; i < 19; ++i) {
+        const char *sp = static_cast<const char *>(h->lat[parity]) + (size_t)i * h->P * h->elem;
+        char *dp = static_cast<char *>(h->lat[parity ^ 1]) + (size_t)i * h->P * h->elem;
+        const long long shift = (long long)(stg::cx_of(i) + stg::cy_of(i) * h->d.nx) * (long long)h->elem;
+        a.srcp[i] = sp;
+        a.srci[i] = sp - shift;
+        a.dstp[i] = dp;
+    }
     a.nx = h->d.nx;
     a.ny = h->d.ny;
     a.nz = h->d.nz;
@@ -334,7 +345,8 @@ cudaError_t enqueue_step(stg_lbm *h, int parity)
         e = stg::launch_inlet(inlet_args(h, parity), h->stream);
         if (e != cudaSuccess) return e;
     }
-    return stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, h->stream);
+    return stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, h->stream, h->side, h->ev_fork,
+                            h->ev_join);
 }
 
 int capture(stg_lbm *h, int parity, int steps, cudaGraphExec_t *out)
@@ -346,7 +358,7 @@ int capture(stg_lbm *h, int parity, int steps, cudaGraphExec_t *out)
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch during capture");
     if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(out, g, 0);
+    e = cudaGraphInstantiate(out, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
     return STG_OK;
@@ -439,6 +451,9 @@ void release(stg_lbm *h)
     h->allocs.clear();
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
     if (h->ev_check) cudaEventDestroy(h->ev_check);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_done) cudaEventDestroy(h->ev_done);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -519,7 +534,12 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
         }
         h->own_stream = true;
     }
+    int lo_prio = 0, hi_prio = 0;  // the edge branch gets the highest priority: its blocks start first
     if (cudaEventCreateWithFlags(&h->ev_check, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&h->h_pinned, 4 * sizeof(double)) != cudaSuccess) {
         h->err = "event / pinned allocation failed";
@@ -623,7 +643,9 @@ int stg_lbm_step_timed(stg_lbm *h, int64_t n, double *ms_step, double *ms_inlet)
         cudaError_t e = cudaEventRecord(ev[3 * s], h->stream);
         if (e == cudaSuccess && h->inout) e = stg::launch_inlet(inlet_args(h, parity), h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], h->stream);
-        if (e == cudaSuccess) e = stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, h->stream);
+        if (e == cudaSuccess)
+            e = stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, h->stream, h->side, h->ev_fork,
+                                 h->ev_join);
         if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], h->stream);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "timed step launch");
         else h->t += 1;

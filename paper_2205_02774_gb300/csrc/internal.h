@@ -20,6 +20,13 @@ struct StepCtl {
 struct StepArgs {
     const void *src;      // post-collision populations of the previous step
     void *dst;            // post-collision populations of this step
+    // per-population plane pointers (kernel parameters, so every address is
+    // one multiply-add of the cell index onto a constant-bank operand):
+    //   srcp[i] = plane i of src, srci[i] = srcp[i] - (c_ix + c_iy nx) elements
+    //   (interior pull), dstp[i] = plane i of dst
+    const void *srcp[19];
+    const void *srci[19];
+    void *dstp[19];
     int nx, ny, nz;
     unsigned P;           // cells per population plane (nx*ny*nz)
     int bc_x, bc_y;       // STG_BC_X_*, STG_BC_Y_*
@@ -64,7 +71,8 @@ struct MassArgs {
 };
 
 // launchers (return the launch status)
-cudaError_t launch_step(const StepArgs &a, int storage, int collision, cudaStream_t s);
+cudaError_t launch_step(const StepArgs &a, int storage, int collision, cudaStream_t s, cudaStream_t side,
+                        cudaEvent_t fork, cudaEvent_t join);
 cudaError_t launch_inlet(const InletArgs &a, cudaStream_t s);
 cudaError_t launch_setup_nodes(int ny, int N, const double *R6, const double *le, const double *leta,
                                const double *lcut, const double *kn, const double *dk, float *a6,

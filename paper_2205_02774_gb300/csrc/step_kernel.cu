@@ -95,18 +95,18 @@ __device__ __forceinline__ void rebuild(float (&g)[Q], float drho, float ux, flo
 
 // Pull of the 19 populations of cell `here` for a warp whose cells and all
 // their x/y neighbours are inside the lattice (no wall, no inlet/outlet lane,
-// no x/y wrap): every source is here - (c_x + c_y nx) - (z shift) in
-// population plane i, a warp-uniform offset.  dzm / dzp are the shifts for
-// c_z = +1 / -1 (nxy and -nxy, or the periodic wrap at z = 0 / nz-1).
+// no x/y wrap): the source of population i is srci[i] + (cell index of the
+// source z row), srci[i] already carrying the -(c_x + c_y nx) shift; hzm /
+// hzp are `here` moved to the z-1 / z+1 row (periodic wrap at the ends).
 template <typename S>
-__device__ __forceinline__ void gather_interior(const S *__restrict__ src, unsigned P, int nx, int dzm, int dzp,
-                                                unsigned here, float (&g)[Q])
+__device__ __forceinline__ void gather_interior(const StepArgs &a, unsigned here, unsigned hzm, unsigned hzp,
+                                                float (&g)[Q])
 {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cz = cz_of(i);
-        const int d = cx_of(i) + cy_of(i) * nx + (cz > 0 ? dzm : (cz < 0 ? dzp : 0));
-        g[i] = Pop<S>::ld(src + (size_t)i * P + (here - d));
+        const unsigned h = cz > 0 ? hzm : (cz < 0 ? hzp : here);
+        g[i] = Pop<S>::ld(static_cast<const S *>(a.srci[i]) + h);
     }
 }
 
@@ -303,7 +303,7 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
             if (!EDGE) {
                 const int dzm = (z == 0) ? -(nz - 1) * nxy : nxy;
                 const int dzp = (z == nz - 1) ? (nz - 1) * nxy : -nxy;
-                gather_interior<S>(src, P, nx, dzm, dzp, here, g);
+                gather_interior<S>(a, here, here - dzm, here - dzp, g);
             } else {
                 const int zm = (z == 0) ? nz - 1 : z - 1;
                 const int zp = (z == nz - 1) ? 0 : z + 1;
@@ -343,7 +343,7 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
             float rho, ux, uy, uz;
             collide<REG, FORCE>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) Pop<S>::st(dst + (size_t)i * P + here, g[i]);
+            for (int i = 0; i < Q; ++i) Pop<S>::st(static_cast<S *>(a.dstp[i]) + here, g[i]);
             if (do_stats) {
                 su0 += ux; su1 += uy; su2 += uz;
                 s00 += ux * ux; s11 += uy * uy; s22 += uz * uz;
@@ -413,14 +413,14 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
 
 // Interior columns: x chunks 1..nxc-2, y = 1..ny-2.
 template <typename S, bool REG, bool FORCE>
-__global__ void __launch_bounds__(BX *BZ, 3) lbm_step_kernel(const StepArgs a)
+__global__ void __launch_bounds__(BX *BZ, 4) lbm_step_kernel(const StepArgs a)
 {
     step_column<S, REG, FORCE, false>(a, blockIdx.x + 1, blockIdx.y + 1);
 }
 
 // Edge columns: x chunks 0 and nxc-1 for every y, then y = 0 and y = ny-1
-// for the interior x chunks.  Launched after the interior kernel; it also
-// advances the device step counter.
+// for the interior x chunks.  It also advances the device step counter
+// (read by the next step's kernels only).
 template <typename S, bool REG, bool FORCE>
 __global__ void __launch_bounds__(BX *BZ, 2) lbm_edge_kernel(const StepArgs a)
 {
@@ -455,30 +455,46 @@ static void edge_counts(int nx, int ny, int &n_interior_x, int &n_interior_y, in
 }
 
 template <typename S, bool REG>
-static void launch_typed(const StepArgs &a, cudaStream_t s)
+static void launch_typed(const StepArgs &a, cudaStream_t s, cudaStream_t side)
 {
     int nix, niy, ne;
     edge_counts(a.nx, a.ny, nix, niy, ne);
     const dim3 block(BX, BZ);
     if (a.has_force) {
+        lbm_edge_kernel<S, REG, true><<<ne, block, 0, side>>>(a);
         if (nix > 0 && niy > 0) lbm_step_kernel<S, REG, true><<<dim3(nix, niy), block, 0, s>>>(a);
-        lbm_edge_kernel<S, REG, true><<<ne, block, 0, s>>>(a);
     } else {
+        lbm_edge_kernel<S, REG, false><<<ne, block, 0, side>>>(a);
         if (nix > 0 && niy > 0) lbm_step_kernel<S, REG, false><<<dim3(nix, niy), block, 0, s>>>(a);
-        lbm_edge_kernel<S, REG, false><<<ne, block, 0, s>>>(a);
     }
 }
 
-cudaError_t launch_step(const StepArgs &a, int storage, int collision, cudaStream_t s)
+// One fused step pass.  With a side stream and two events the edge columns
+// run on a forked branch concurrently with the interior columns (both read
+// only the previous lattice and write disjoint cells); `s` waits for both.
+cudaError_t launch_step(const StepArgs &a, int storage, int collision, cudaStream_t s, cudaStream_t side,
+                        cudaEvent_t fork, cudaEvent_t join)
 {
-    if (storage == 0) {
-        if (collision == 0) launch_typed<float, true>(a, s);
-        else launch_typed<float, false>(a, s);
-    } else {
-        if (collision == 0) launch_typed<__half, true>(a, s);
-        else launch_typed<__half, false>(a, s);
+    cudaError_t e = cudaSuccess;
+    const bool forked = side != nullptr && fork != nullptr && join != nullptr;
+    if (forked) {
+        if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
     }
-    return cudaGetLastError();
+    cudaStream_t es = forked ? side : s;
+    if (storage == 0) {
+        if (collision == 0) launch_typed<float, true>(a, s, es);
+        else launch_typed<float, false>(a, s, es);
+    } else {
+        if (collision == 0) launch_typed<__half, true>(a, s, es);
+        else launch_typed<__half, false>(a, s, es);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (forked) {
+        if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------
