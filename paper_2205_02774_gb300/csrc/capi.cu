@@ -57,7 +57,9 @@ struct stg_lbm {
     double mass0 = 0.0;
     int sticky = STG_OK;
     std::string err;
-    cudaGraphExec_t g_single[2] = {nullptr, nullptr};
+    // single steps by [parity][sampling step]; blocks of block_steps steps that
+    // start at a step index divisible by the sampling period, by parity
+    cudaGraphExec_t g_single[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     cudaGraphExec_t g_block[2] = {nullptr, nullptr};
     int block_steps = 16;
     stg_info info{};
@@ -289,6 +291,7 @@ stg::StepArgs step_args(const stg_lbm *h, int parity)
         const long long shift = (long long)(stg::cx_of(i) + stg::cy_of(i) * h->d.nx) * (long long)h->elem;
         a.srcp[i] = sp;
         a.srci[i] = sp - shift;
+        a.srcy[i] = sp - (long long)stg::cy_of(i) * h->d.nx * (long long)h->elem;
         a.dstp[i] = dp;
     }
     a.nx = h->d.nx;
@@ -338,23 +341,37 @@ stg::InletArgs inlet_args(const stg_lbm *h, int parity)
     return a;
 }
 
-cudaError_t enqueue_step(stg_lbm *h, int parity)
+bool is_stats_step(const stg_lbm *h, int64_t t)
+{
+    return h->d.stats_every > 0 && (t + 1) % h->d.stats_every == 0;
+}
+
+// one step with the given parity (the device reads the step index itself);
+// `stats` selects the sampling-step kernel variant
+cudaError_t enqueue_step(stg_lbm *h, int parity, bool stats)
 {
     cudaError_t e = cudaSuccess;
     if (h->inout) {
         e = stg::launch_inlet(inlet_args(h, parity), h->stream);
         if (e != cudaSuccess) return e;
     }
-    return stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, h->stream, h->side, h->ev_fork,
-                            h->ev_join);
+    return stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, stats, h->stream, h->side,
+                            h->ev_fork, h->ev_join);
 }
 
-int capture(stg_lbm *h, int parity, int steps, cudaGraphExec_t *out)
+// Graph of `steps` steps starting with parity p0.  single_stats >= 0: one
+// step with that sampling flag; otherwise step s samples when (s + 1) is a
+// multiple of the sampling period (a block that starts at an aligned index).
+int capture(stg_lbm *h, int p0, int steps, int single_stats, cudaGraphExec_t *out)
 {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int s = 0; s < steps && e == cudaSuccess; ++s) e = enqueue_step(h, (parity + s) & 1);
+    for (int s = 0; s < steps && e == cudaSuccess; ++s) {
+        const bool st = single_stats >= 0 ? single_stats != 0
+                                          : (h->d.stats_every > 0 && (s + 1) % h->d.stats_every == 0);
+        e = enqueue_step(h, (p0 + s) & 1, st);
+    }
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch during capture");
     if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
@@ -441,7 +458,8 @@ void release(stg_lbm *h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (int p = 0; p < 2; ++p) {
-        if (h->g_single[p]) cudaGraphExecDestroy(h->g_single[p]);
+        for (int q = 0; q < 2; ++q)
+            if (h->g_single[p][q]) cudaGraphExecDestroy(h->g_single[p][q]);
         if (h->g_block[p]) cudaGraphExecDestroy(h->g_block[p]);
     }
     for (auto &a : h->allocs) {
@@ -590,9 +608,14 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
     if (rc) return bail(rc);
     rc = compute_mass(h, &h->mass0);
     if (rc) return bail(rc);
+    // block length: a multiple of the sampling period, at least 16 steps
+    const int k = domain->stats_every;
+    h->block_steps = k > 0 ? k * ((16 + k - 1) / k) : 16;
+    if (h->block_steps > 256) h->block_steps = 0;  // very long sampling periods: single-step graphs only
     for (int p = 0; p < 2 && rc == STG_OK; ++p) {
-        rc = capture(h, p, 1, &h->g_single[p]);
-        if (rc == STG_OK) rc = capture(h, p, h->block_steps, &h->g_block[p]);
+        rc = capture(h, p, 1, 0, &h->g_single[p][0]);
+        if (rc == STG_OK && k > 0) rc = capture(h, p, 1, 1, &h->g_single[p][1]);
+        if (rc == STG_OK && h->block_steps > 0) rc = capture(h, p, h->block_steps, -1, &h->g_block[p]);
     }
     if (rc) return bail(rc);
     *out = h;
@@ -606,15 +629,17 @@ int stg_lbm_step(stg_lbm *h, int64_t n)
     int rc = poll_check(h);
     if (rc) return rc;
     if (h->sticky) return fail(h, h->sticky, "an earlier check failed; reset the state first");
+    const int per = h->d.stats_every;
     while (n > 0) {
         cudaGraphExec_t g;
-        int k;
-        if (n >= h->block_steps) {
-            g = h->g_block[h->t & 1];
+        int k = 1;
+        const int par = (int)(h->t & 1);
+        const bool aligned = per <= 0 || h->t % per == 0;
+        if (h->block_steps > 0 && n >= h->block_steps && aligned) {
+            g = h->g_block[par];
             k = h->block_steps;
         } else {
-            g = h->g_single[h->t & 1];
-            k = 1;
+            g = h->g_single[par][is_stats_step(h, h->t) ? 1 : 0];
         }
         CK(cudaGraphLaunch(g, h->stream));
         h->t += k;
@@ -644,8 +669,8 @@ int stg_lbm_step_timed(stg_lbm *h, int64_t n, double *ms_step, double *ms_inlet)
         if (e == cudaSuccess && h->inout) e = stg::launch_inlet(inlet_args(h, parity), h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], h->stream);
         if (e == cudaSuccess)
-            e = stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, h->stream, h->side, h->ev_fork,
-                                 h->ev_join);
+            e = stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, is_stats_step(h, h->t),
+                                 h->stream, h->side, h->ev_fork, h->ev_join);
         if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], h->stream);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "timed step launch");
         else h->t += 1;

@@ -24,9 +24,13 @@ struct StepArgs {
     // one multiply-add of the cell index onto a constant-bank operand):
     //   srcp[i] = plane i of src, srci[i] = srcp[i] - (c_ix + c_iy nx) elements
     //   (interior pull), dstp[i] = plane i of dst
+    //   srcy[i] = srcp[i] - c_iy nx elements (two-cells-per-thread pull)
     const void *srcp[19];
     const void *srci[19];
+    const void *srcy[19];
     void *dstp[19];
+    int il, ir;             // 32-wide x chunks [il, ir) of rows 1..ny-2 belong to the interior kernel
+    unsigned total_blocks;  // blocks of all step kernels of the pass (mass-check completion count)
     int nx, ny, nz;
     unsigned P;           // cells per population plane (nx*ny*nz)
     int bc_x, bc_y;       // STG_BC_X_*, STG_BC_Y_*
@@ -71,8 +75,10 @@ struct MassArgs {
 };
 
 // launchers (return the launch status)
-cudaError_t launch_step(const StepArgs &a, int storage, int collision, cudaStream_t s, cudaStream_t side,
-                        cudaEvent_t fork, cudaEvent_t join);
+// `stats` must be true exactly on sampling steps ((t + 1) % stats_every == 0);
+// the host tracks t and decides.
+cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, cudaStream_t s,
+                        cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 cudaError_t launch_inlet(const InletArgs &a, cudaStream_t s);
 cudaError_t launch_setup_nodes(int ny, int N, const double *R6, const double *le, const double *leta,
                                const double *lcut, const double *kn, const double *dk, float *a6,

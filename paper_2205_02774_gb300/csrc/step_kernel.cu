@@ -18,80 +18,12 @@
 
 #include "d3q19.cuh"
 #include "internal.h"
+#include "lbm_cell.cuh"
 
 namespace stg {
 
 constexpr int BX = 32;
 constexpr int BZ = 8;
-
-// Both storage formats hold the shifted population g_i = f_i - w_i, and all
-// arithmetic below works on g: the rest weights never enter a sum, so FP32
-// rounding acts on the small fluctuating part only (no weight-rounding bias
-// in the mass, no loss of the low-order bits of slow flows).
-template <typename S>
-struct Pop;
-
-template <>
-struct Pop<float> {
-    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
-    static __device__ __forceinline__ void st(float *p, float g) { __stcs(p, g); }
-};
-
-template <>
-struct Pop<__half> {
-    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
-    static __device__ __forceinline__ void st(__half *p, float g) { __stcs(p, __float2half_rn(g)); }
-};
-
-// shifted equilibrium g^eq_i = f^eq_i - w_i = w_i [drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)]
-__device__ __forceinline__ float geq(float w, float drho, float rho, float cu, float uu)
-{
-    return w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
-}
-
-// Regularized rebuild of a boundary node (eqs. f_i, f_i_neq, pi_neq,
-// unknown_neq, bc_eq): the unknown directions (sign(c_x) == SGN) take the
-// non-equilibrium part of their opposite; all 19 are then replaced by
-// f^eq + w_i/(2 cs^4) Q_i : Pi_neq.
-template <int SGN>
-__device__ __forceinline__ void rebuild(float (&g)[Q], float drho, float ux, float uy, float uz)
-{
-    const float rho = 1.0f + drho;
-    const float uu = ux * ux + uy * uy + uz * uz;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        if (cx != SGN) g[i] = g[i] - geq(w_of(i), drho, rho, cx * ux + cy * uy + cz * uz, uu);
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-        if (cx_of(i) == SGN) g[i] = g[opp_of(i)];
-    float s = 0.f, pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const float v = g[i];
-        s += v;
-        if (cx * cx) pxx += v;
-        if (cy * cy) pyy += v;
-        if (cz * cz) pzz += v;
-        if (cx * cy) pxy += cx * cy * v;
-        if (cx * cz) pxz += cx * cz * v;
-        if (cy * cz) pyz += cy * cz * v;
-    }
-    // Pi_neq = sum_i Q_i f_i^neq with Q_i = c_i c_i - I/3
-    pxx -= s * (1.0f / 3.0f);
-    pyy -= s * (1.0f / 3.0f);
-    pzz -= s * (1.0f / 3.0f);
-    const float tr3 = (pxx + pyy + pzz) * (1.0f / 3.0f);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const float cpc = cx * cx * pxx + cy * cy * pyy + cz * cz * pzz
-                        + 2.0f * (cx * cy * pxy + cx * cz * pxz + cy * cz * pyz);
-        g[i] = geq(w_of(i), drho, rho, cx * ux + cy * uy + cz * uz, uu) + 4.5f * w_of(i) * (cpc - tr3);
-    }
-}
 
 // Pull of the 19 populations of cell `here` for a warp whose cells and all
 // their x/y neighbours are inside the lattice (no wall, no inlet/outlet lane,
@@ -132,128 +64,54 @@ __device__ __forceinline__ void gather_general(const S *__restrict__ src, unsign
     }
 }
 
-// Moments, Smagorinsky relaxation and collision of one cell, in shifted
-// variables, written over opposite pairs (i, i+1), c_{i+1} = -c_i: every
-// term of the update is either even in c (equilibrium second order,
-// regularized non-equilibrium, force x velocity) or odd (first order), so
-// each pair costs one even and one odd part.
-template <bool REG, bool FORCE>
-__device__ __forceinline__ void collide(float (&g)[Q], float tau0, float kq, float Fx, float Fy, float Fz,
-                                        float &rho_o, float &ux_o, float &uy_o, float &uz_o)
+// Deterministic FP64 mass of the pass: each block leaves its partial at
+// mass_partial[part] (and 0 at `zero` when it spans two 32-wide columns); the
+// last of all total_blocks blocks adds the nxc*ny partials in index order.
+__device__ __forceinline__ void mass_finish(const StepArgs &a, float sdr, int part, int zero)
 {
-    float s[9], d[9];
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-        s[p] = g[2 * p + 1] + g[2 * p + 2];
-        d[p] = g[2 * p + 1] - g[2 * p + 2];
+    __shared__ double rd[BX * BZ];
+    __shared__ int s_last;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    rd[tid] = (double)sdr;
+    __syncthreads();
+    for (int off = BZ * BX / 2; off > 0; off >>= 1) {
+        if (tid < off) rd[tid] += rd[tid + off];
+        __syncthreads();
     }
-    float drho = g[0], jx = 0.f, jy = 0.f, jz = 0.f;
-    float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-        const int i = 2 * p + 1;
-        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        drho += s[p];
-        if (cx) jx += cx * d[p];
-        if (cy) jy += cy * d[p];
-        if (cz) jz += cz * d[p];
-        if (cx) pxx += s[p];
-        if (cy) pyy += s[p];
-        if (cz) pzz += s[p];
-        if (cx * cy) pxy += cx * cy * s[p];
-        if (cx * cz) pxz += cx * cz * s[p];
-        if (cy * cz) pyz += cy * cz * s[p];
+    const unsigned nparts = (unsigned)((a.nx + BX - 1) / BX) * a.ny;
+    if (tid == 0) {
+        a.mass_partial[part] = rd[0];
+        if (zero >= 0) a.mass_partial[zero] = 0.0;
+        __threadfence();
+        const unsigned prev = atomicAdd(a.mass_counter, 1u);
+        s_last = (prev == a.total_blocks - 1);
     }
-    const float rho = 1.0f + drho;
-    const float irho = 1.0f / rho;
-    const float ux = (FORCE ? jx + 0.5f * Fx : jx) * irho;
-    const float uy = (FORCE ? jy + 0.5f * Fy : jy) * irho;
-    const float uz = (FORCE ? jz + 0.5f * Fz : jz) * irho;
-    // Pi_neq = Pi - rho (cs^2 I + u u) = sum c c g - drho/3 I - rho u u
-    const float rux = rho * ux, ruy = rho * uy, ruz = rho * uz;
-    const float nxx = pxx - drho * (1.0f / 3.0f) - rux * ux;
-    const float nyy = pyy - drho * (1.0f / 3.0f) - ruy * uy;
-    const float nzz = pzz - drho * (1.0f / 3.0f) - ruz * uz;
-    const float nxy = pxy - rux * uy;
-    const float nxz = pxz - rux * uz;
-    const float nyz = pyz - ruy * uz;
-    const float qh = sqrtf(nxx * nxx + nyy * nyy + nzz * nzz + 2.0f * (nxy * nxy + nxz * nxz + nyz * nyz));
-    // eq. (tau_eff), c = 1: tau = tau0/2 + sqrt((tau0 rho)^2 + 18 sqrt2 C Q^1/2)/(2 rho)
-    const float tau = 0.5f * tau0 + 0.5f * sqrtf(tau0 * tau0 + kq * qh * irho * irho);
-    const float om = 1.0f / tau;
-    const float uu = ux * ux + uy * uy + uz * uz;
-    const float tr3 = (nxx + nyy + nzz) * (1.0f / 3.0f);
-    const float uF = FORCE ? ux * Fx + uy * Fy + uz * Fz : 0.f;
-    const float kneq = REG ? 4.5f * (1.0f - om) : 0.f;   // (1 - 1/tau) w_i/(2 cs^4) / w_i
-    const float kf = FORCE ? (1.0f - 0.5f * om) : 0.f;   // Guo prefactor
-    // base of the even part shared by all directions: drho - 1.5 rho u.u
-    const float e0 = drho - 1.5f * rho * uu;
-    // rest population
-    {
-        const float w = w_of(0);
-        float ge = w * e0;
-        if (REG) {
-            float go = ge - w * kneq * tr3;
-            if (FORCE) go += kf * w * (-3.0f * uF);
-            g[0] = go;
-        } else {
-            float go = g[0] - om * (g[0] - ge);
-            if (FORCE) go += kf * w * (-3.0f * uF);
-            g[0] = go;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        double acc = 0.0;
+        for (unsigned k = tid; k < nparts; k += BZ * BX) acc += __ldcg(a.mass_partial + k);
+        rd[tid] = acc;
+        __syncthreads();
+        for (int off = BZ * BX / 2; off > 0; off >>= 1) {
+            if (tid < off) rd[tid] += rd[tid + off];
+            __syncthreads();
+        }
+        if (tid == 0) {
+            a.mass_out[0] = rd[0] + (double)a.P;
+            *a.mass_counter = 0u;
         }
     }
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-        const int i = 2 * p + 1;
-        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const float w = w_of(i);
-        const float cu = cx * ux + cy * uy + cz * uz;
-        // even and odd parts of the shifted equilibrium: w [e0 + 4.5 rho cu^2] +- w 3 rho cu
-        float ev = w * (e0 + 4.5f * rho * cu * cu);
-        float od = w * 3.0f * rho * cu;
-        if (REG) {
-            const float cpc = cx * cx * nxx + cy * cy * nyy + cz * cz * nzz
-                            + 2.0f * (cx * cy * nxy + cx * cz * nxz + cy * cz * nyz);
-            ev += w * kneq * (cpc - tr3);
-        }
-        if (FORCE) {
-            const float cF = cx * Fx + cy * Fy + cz * Fz;
-            // Guo term, eq. (bodyforce): even part 9 (c.u)(c.F) - 3 u.F, odd part 3 c.F
-            ev += kf * w * (9.0f * cu * cF - 3.0f * uF);
-            od += kf * w * 3.0f * cF;
-            // regularized: keep the first-order neq part a1 = -F/2
-            if (REG) od -= (1.0f - om) * 1.5f * w * cF;
-        }
-        if (REG) {
-            g[i] = ev + od;
-            g[i + 1] = ev - od;
-        } else {
-            g[i] = g[i] - om * (g[i] - (ev + od));
-            g[i + 1] = g[i + 1] - om * (g[i + 1] - (ev - od));
-            if (FORCE) {
-                // the Guo parts were folded into ev/od above; undo the relaxation on them
-                const float cF = cx * Fx + cy * Fy + cz * Fz;
-                const float fe = kf * w * (9.0f * cu * cF - 3.0f * uF), fo = kf * w * 3.0f * cF;
-                g[i] += (1.0f - om) * (fe + fo);
-                g[i + 1] += (1.0f - om) * (fe - fo);
-            }
-        }
-    }
-    rho_o = rho;
-    ux_o = ux;
-    uy_o = uy;
-    uz_o = uz;
 }
 
-// One block = one (x chunk, y) column over all z.  EDGE selects the general
-// pull (walls, wraps, inlet/outlet rebuild); the interior variant only sees
-// columns whose x chunk is neither the first nor the last and whose y has
-// both neighbours inside the lattice.
+// One block = one 32-wide (x chunk, y) column over all z, one cell per
+// thread.  EDGE selects the general pull (walls, wraps, inlet/outlet
+// rebuild); the interior variant only sees columns whose x chunk is neither
+// the first nor the last and whose y has both neighbours inside the lattice.
 template <typename S, bool REG, bool FORCE, bool EDGE>
 __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
 {
     const S *__restrict__ src = static_cast<const S *>(a.src);
-    S *__restrict__ dst = static_cast<S *>(a.dst);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int nxy = nx * ny;
     const unsigned P = a.P;
@@ -371,71 +229,215 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
             }
         }
     }
-
-    if (do_check) {
-        // block partial, then the last of all nxc*ny blocks (both kernels)
-        // adds the partials in index order: deterministic FP64 mass
-        __shared__ double rd[BZ * BX];
-        __shared__ int s_last;
-        const int tid = threadIdx.y * BX + threadIdx.x;
-        rd[tid] = (double)sdr;
-        __syncthreads();
-        for (int off = BZ * BX / 2; off > 0; off >>= 1) {
-            if (tid < off) rd[tid] += rd[tid + off];
-            __syncthreads();
-        }
-        const int nxc = (nx + BX - 1) / BX;
-        const unsigned nblocks = (unsigned)nxc * ny;
-        if (tid == 0) {
-            a.mass_partial[(size_t)y * nxc + bx] = rd[0];
-            __threadfence();
-            const unsigned prev = atomicAdd(a.mass_counter, 1u);
-            s_last = (prev == nblocks - 1);
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            double acc = 0.0;
-            for (unsigned k = tid; k < nblocks; k += BZ * BX) acc += __ldcg(a.mass_partial + k);
-            rd[tid] = acc;
-            __syncthreads();
-            for (int off = BZ * BX / 2; off > 0; off >>= 1) {
-                if (tid < off) rd[tid] += rd[tid + off];
-                __syncthreads();
-            }
-            if (tid == 0) {
-                a.mass_out[0] = rd[0] + (double)P;
-                *a.mass_counter = 0u;
-            }
-        }
-    }
+    if (do_check) mass_finish(a, sdr, y * ((nx + BX - 1) / BX) + bx, -1);
 }
 
-// Interior columns: x chunks 1..nxc-2, y = 1..ny-2.
+// Scalar interior columns: x chunks [il, ir), y = 1..ny-2 (odd nx or narrow lattices).
 template <typename S, bool REG, bool FORCE>
 __global__ void __launch_bounds__(BX *BZ, 4) lbm_step_kernel(const StepArgs a)
 {
-    step_column<S, REG, FORCE, false>(a, blockIdx.x + 1, blockIdx.y + 1);
+    step_column<S, REG, FORCE, false>(a, a.il + blockIdx.x, blockIdx.y + 1);
 }
 
-// Edge columns: x chunks 0 and nxc-1 for every y, then y = 0 and y = ny-1
-// for the interior x chunks.  It also advances the device step counter
-// (read by the next step's kernels only).
+// ---------------------------------------------------------------------------
+// Two cells per thread: lane l of a warp owns cells (x, x+1), x = 64 c + 2 l,
+// so every population row is read and written as aligned 8-byte (FP32) or
+// 4-byte (FP16) pairs, 256 B / 128 B per warp instruction.  A pull with
+// c_x = +1 needs (x-1, x): the x-1 value is the upper half of the left lane's
+// pair (warp shuffle), lane 0 reads it directly; c_x = -1 mirrors this.
+template <typename S>
+struct Pair;
+
+template <>
+struct Pair<float> {
+    using raw = float2;
+    static __device__ __forceinline__ raw ld(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+    static __device__ __forceinline__ float lo(raw v) { return v.x; }
+    static __device__ __forceinline__ float hi(raw v) { return v.y; }
+    // (x-1, x) from the left lane's pair (x-2, x-1) and ours (x, x+1)
+    static __device__ __forceinline__ raw shift_in_left(raw cur, const float *p_xm1, int lane)
+    {
+        float l = __shfl_up_sync(0xffffffffu, cur.y, 1);
+        if (lane == 0) l = __ldg(p_xm1);
+        return make_float2(l, cur.x);
+    }
+    // (x+1, x+2) from ours (x, x+1) and the right lane's (x+2, x+3)
+    static __device__ __forceinline__ raw shift_in_right(raw cur, const float *p_xp2, int lane)
+    {
+        float r = __shfl_down_sync(0xffffffffu, cur.x, 1);
+        if (lane == 31) r = __ldg(p_xp2);
+        return make_float2(cur.y, r);
+    }
+    static __device__ __forceinline__ void st(float *p, float a, float b)
+    {
+        __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
+    }
+};
+
+template <>
+struct Pair<__half> {
+    using raw = unsigned;  // two binary16: low half = x, high half = x+1
+    static __device__ __forceinline__ raw ld(const __half *p) { return __ldg(reinterpret_cast<const unsigned *>(p)); }
+    static __device__ __forceinline__ float lo(raw v) { return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu))); }
+    static __device__ __forceinline__ float hi(raw v) { return __half2float(__ushort_as_half((unsigned short)(v >> 16))); }
+    static __device__ __forceinline__ raw shift_in_left(raw cur, const __half *p_xm1, int lane)
+    {
+        unsigned l = __shfl_up_sync(0xffffffffu, cur, 1);
+        if (lane == 0) l = (unsigned)__half_as_ushort(__ldg(p_xm1)) << 16;
+        return __byte_perm(l, cur, 0x5432);
+    }
+    static __device__ __forceinline__ raw shift_in_right(raw cur, const __half *p_xp2, int lane)
+    {
+        unsigned r = __shfl_down_sync(0xffffffffu, cur, 1);
+        if (lane == 31) r = (unsigned)__half_as_ushort(__ldg(p_xp2));
+        return __byte_perm(cur, r, 0x5432);
+    }
+    static __device__ __forceinline__ void st(__half *p, float a, float b)
+    {
+        const unsigned v = (unsigned)__half_as_ushort(__float2half_rn(a)) |
+                           ((unsigned)__half_as_ushort(__float2half_rn(b)) << 16);
+        __stcs(reinterpret_cast<unsigned *>(p), v);
+    }
+};
+
+// write a result into the first cell of a raw pair / read it back
+__device__ __forceinline__ float2 pack_lo(float2 v, float a) { return make_float2(a, v.y); }
+__device__ __forceinline__ float lo_of(float2 v) { return v.x; }
+// FP16: the low half keeps the already rounded binary16 of the first cell's result
+__device__ __forceinline__ unsigned pack_lo(unsigned v, float a)
+{
+    return (v & 0xffff0000u) | (unsigned)__half_as_ushort(__float2half_rn(a));
+}
+__device__ __forceinline__ float lo_of(unsigned v) { return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu))); }
+
+// z loop of one pair column; STATS adds the per-cell velocity sums to the
+// block's shared-memory slots (sampling steps only).  Returns the thread's
+// sum of rho - 1 when CHECK.
+template <typename S, bool REG, bool FORCE, bool STATS>
+__device__ __forceinline__ float pair_loop(const StepArgs &a, float (*sacc)[9][2 * BX], int c, int y)
+{
+    using PR = Pair<S>;
+    using raw = typename PR::raw;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int nxy = nx * ny;
+    const int lane = threadIdx.x, tz = threadIdx.y;
+    const int x = 64 * c + 2 * lane;
+    const float tau0 = a.tau0, kq = a.kq;
+    const float Fx = a.Fx, Fy = a.Fy, Fz = a.Fz;
+    const S *__restrict__ sbase = static_cast<const S *>(a.src);
+    S *__restrict__ dbase = static_cast<S *>(a.dst);
+    float sdr = 0.f;
+    for (int z = tz; z < nz; z += BZ) {
+        // Plane offsets i P are recomputed in every iteration from an opaque
+        // copy of P: hoisting 19 + 19 plane pointers out of the loop would
+        // cost 76 registers.  Element offsets are 32-bit (19 P < 2^32).
+        unsigned Pv, nxv;
+        asm volatile("mov.u32 %0, %1;" : "=r"(Pv) : "r"(a.P));
+        asm volatile("mov.u32 %0, %1;" : "=r"(nxv) : "r"((unsigned)nx));
+        const unsigned here = ((unsigned)z * ny + y) * nx + x;
+        const unsigned hzm = here - ((z == 0) ? -(nz - 1) * nxy : nxy);
+        const unsigned hzp = here - ((z == nz - 1) ? (nz - 1) * nxy : -nxy);
+        raw v[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = cx_of(i), cz = cz_of(i), cy = cy_of(i);
+            const unsigned h = cz > 0 ? hzm : (cz < 0 ? hzp : here);
+            const S *row = sbase + (i * Pv + h - cy * nxv);  // (x, y - c_y, z - c_z)
+            const raw cur = PR::ld(row);
+            if (cx == 0) v[i] = cur;
+            else if (cx > 0) v[i] = PR::shift_in_left(cur, row - 1, lane);
+            else v[i] = PR::shift_in_right(cur, row + 2, lane);
+        }
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            float g[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[i] = half ? PR::hi(v[i]) : PR::lo(v[i]);
+            float rho, ux, uy, uz;
+            collide<REG, FORCE>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz);
+            if (half == 0) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) v[i] = pack_lo(v[i], g[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) PR::st(dbase + (i * Pv + here), lo_of(v[i]), g[i]);
+            }
+            if (STATS) {
+                float *s = &sacc[tz][0][2 * lane + half];
+                s[0 * 2 * BX] += ux; s[1 * 2 * BX] += uy; s[2 * 2 * BX] += uz;
+                s[3 * 2 * BX] += ux * ux; s[4 * 2 * BX] += uy * uy; s[5 * 2 * BX] += uz * uz;
+                s[6 * 2 * BX] += ux * uy; s[7 * 2 * BX] += ux * uz; s[8 * 2 * BX] += uy * uz;
+            }
+            sdr += rho - 1.0f;
+        }
+    }
+    return sdr;
+}
+
+// STATS is chosen on the host (it knows the step count): the sampling-step
+// variant is a separate instantiation, so the plain z loop keeps its
+// registers free of the statistics bookkeeping.
+template <typename S, bool REG, bool FORCE, bool STATS>
+__global__ void __launch_bounds__(BX *BZ, 3) lbm_pair_kernel(const StepArgs a)
+{
+    __shared__ float sacc[STATS ? BZ : 1][9][2 * BX];  // per-thread statistics slots
+    const int nx = a.nx, ny = a.ny;
+    const int c = a.il / 2 + blockIdx.x;   // 64-wide chunk
+    const int y = blockIdx.y + 1;
+    const int lane = threadIdx.x, tz = threadIdx.y;
+    const long long t = a.ctl->t[a.parity];
+    const bool do_check = a.check_every > 0 && ((t + 1) % a.check_every) == 0;
+    if (STATS) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            sacc[tz][q][2 * lane] = 0.f;
+            sacc[tz][q][2 * lane + 1] = 0.f;
+        }
+    }
+    const float sdr = pair_loop<S, REG, FORCE, STATS>(a, sacc, c, y);
+    if (STATS) {
+        __syncthreads();
+        if (tz == 0) {
+            const size_t m = (size_t)nx * ny;
+#pragma unroll
+            for (int k2 = 0; k2 < 2; ++k2) {
+                const int col = 2 * lane + k2;
+                const size_t xy = (size_t)y * nx + 64 * c + col;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    double s = 0.0;
+                    for (int k = 0; k < BZ; ++k) s += (double)sacc[k][q][col];
+                    if (q < 3) a.stat_mean[q * m + xy] += s;
+                    else a.stat_rey[(q - 3) * m + xy] += s;
+                }
+            }
+        }
+    }
+    if (do_check) {
+        const int nxc = (nx + BX - 1) / BX;
+        mass_finish(a, sdr, y * nxc + 2 * c, y * nxc + 2 * c + 1);
+    }
+}
+
+// Edge columns (32 wide, one cell per thread, general pull): every chunk of
+// rows 0 and ny-1, and the chunks outside [il, ir) of rows 1..ny-2.  Block 0
+// also advances the device step counter (read by the next step only).
 template <typename S, bool REG, bool FORCE>
 __global__ void __launch_bounds__(BX *BZ, 2) lbm_edge_kernel(const StepArgs a)
 {
     const int nxc = (a.nx + BX - 1) / BX;
     const int b = blockIdx.x;
-    const int nedge_x = (nxc > 1 ? 2 : 1) * a.ny;
+    const int nwall = (a.ny >= 2 ? 2 : 1) * nxc;
     int bx, y;
-    if (b < nedge_x) {
-        bx = (nxc > 1 && b >= a.ny) ? nxc - 1 : 0;
-        y = (nxc > 1 && b >= a.ny) ? b - a.ny : b;
+    if (b < nwall) {
+        y = (b < nxc) ? 0 : a.ny - 1;
+        bx = b % nxc;
     } else {
-        const int r = b - nedge_x;       // interior x chunks, rows y = 0 and y = ny-1
-        const int nin = nxc - 2;
-        bx = 1 + (r % nin);
-        y = (r / nin == 0) ? 0 : a.ny - 1;
+        const int emid = nxc - (a.ir - a.il);
+        const int r = b - nwall;
+        y = 1 + r / emid;
+        const int k = r % emid;
+        bx = k < a.il ? k : a.ir + (k - a.il);
     }
     const long long t = a.ctl->t[a.parity];
     step_column<S, REG, FORCE, true>(a, bx, y);
@@ -444,36 +446,76 @@ __global__ void __launch_bounds__(BX *BZ, 2) lbm_edge_kernel(const StepArgs a)
 
 int step_grid_blocks(int nx, int ny) { return ((nx + BX - 1) / BX) * ny; }
 
-// interior grid (x chunks 1..nxc-2) x (y 1..ny-2) and the number of edge
-// columns; interior + edge = nxc * ny, each column exactly once.
-static void edge_counts(int nx, int ny, int &n_interior_x, int &n_interior_y, int &n_edge)
+// Split of the lattice between the interior kernel (pair or scalar) and the
+// edge kernel.  pair: nx even and at least three 64-wide chunks.
+struct Split {
+    bool pair;
+    int il, ir;           // interior 32-wide chunks [il, ir) of rows 1..ny-2
+    int gx, gy;           // interior grid
+    int n_edge;
+};
+
+static Split split_of(int nx, int ny, int nz)
 {
+    Split sp{};
     const int nxc = (nx + BX - 1) / BX;
-    n_interior_x = nxc > 2 ? nxc - 2 : 0;
-    n_interior_y = ny > 2 ? ny - 2 : 0;
-    n_edge = (nxc > 1 ? 2 : 1) * ny + (ny >= 2 ? 2 : 1) * n_interior_x;
+    const int C = nx / 64;
+    sp.pair = (nx % 2 == 0) && C >= 3 && ny >= 3 && 19.0 * nx * ny * nz < 4294967296.0;
+    if (sp.pair) {
+        sp.il = 2;
+        sp.ir = 2 * (C - 1);
+        sp.gx = C - 2;
+    } else if (nxc >= 3 && ny >= 3) {
+        sp.il = 1;
+        sp.ir = nxc - 1;
+        sp.gx = nxc - 2;
+    } else {
+        sp.il = sp.ir = 0;
+        sp.gx = 0;
+    }
+    sp.gy = (ny >= 3 && sp.gx > 0) ? ny - 2 : 0;
+    if (sp.gy == 0) {
+        sp.il = sp.ir = 0;
+        sp.gx = 0;
+    }
+    const int nwall = (ny >= 2 ? 2 : 1) * nxc;
+    sp.n_edge = nwall + (ny > 2 ? ny - 2 : 0) * (nxc - (sp.ir - sp.il));
+    return sp;
+}
+
+template <typename S, bool REG, bool FORCE>
+static void launch_forced(StepArgs a, const Split &sp, bool stats, cudaStream_t s, cudaStream_t side)
+{
+    const dim3 block(BX, BZ);
+    lbm_edge_kernel<S, REG, FORCE><<<sp.n_edge, block, 0, side>>>(a);
+    if (sp.gx > 0 && sp.gy > 0) {
+        const dim3 grid(sp.gx, sp.gy);
+        if (sp.pair) {
+            if (stats) lbm_pair_kernel<S, REG, FORCE, true><<<grid, block, 0, s>>>(a);
+            else lbm_pair_kernel<S, REG, FORCE, false><<<grid, block, 0, s>>>(a);
+        } else {
+            lbm_step_kernel<S, REG, FORCE><<<grid, block, 0, s>>>(a);
+        }
+    }
 }
 
 template <typename S, bool REG>
-static void launch_typed(const StepArgs &a, cudaStream_t s, cudaStream_t side)
+static void launch_typed(const StepArgs &a0, bool stats, cudaStream_t s, cudaStream_t side)
 {
-    int nix, niy, ne;
-    edge_counts(a.nx, a.ny, nix, niy, ne);
-    const dim3 block(BX, BZ);
-    if (a.has_force) {
-        lbm_edge_kernel<S, REG, true><<<ne, block, 0, side>>>(a);
-        if (nix > 0 && niy > 0) lbm_step_kernel<S, REG, true><<<dim3(nix, niy), block, 0, s>>>(a);
-    } else {
-        lbm_edge_kernel<S, REG, false><<<ne, block, 0, side>>>(a);
-        if (nix > 0 && niy > 0) lbm_step_kernel<S, REG, false><<<dim3(nix, niy), block, 0, s>>>(a);
-    }
+    const Split sp = split_of(a0.nx, a0.ny, a0.nz);
+    StepArgs a = a0;
+    a.il = sp.il;
+    a.ir = sp.ir;
+    a.total_blocks = (unsigned)(sp.n_edge + sp.gx * sp.gy);
+    if (a.has_force) launch_forced<S, REG, true>(a, sp, stats, s, side);
+    else launch_forced<S, REG, false>(a, sp, stats, s, side);
 }
 
 // One fused step pass.  With a side stream and two events the edge columns
 // run on a forked branch concurrently with the interior columns (both read
 // only the previous lattice and write disjoint cells); `s` waits for both.
-cudaError_t launch_step(const StepArgs &a, int storage, int collision, cudaStream_t s, cudaStream_t side,
-                        cudaEvent_t fork, cudaEvent_t join)
+cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, cudaStream_t s,
+                        cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
 {
     cudaError_t e = cudaSuccess;
     const bool forked = side != nullptr && fork != nullptr && join != nullptr;
@@ -483,11 +525,11 @@ cudaError_t launch_step(const StepArgs &a, int storage, int collision, cudaStrea
     }
     cudaStream_t es = forked ? side : s;
     if (storage == 0) {
-        if (collision == 0) launch_typed<float, true>(a, s, es);
-        else launch_typed<float, false>(a, s, es);
+        if (collision == 0) launch_typed<float, true>(a, stats, s, es);
+        else launch_typed<float, false>(a, stats, s, es);
     } else {
-        if (collision == 0) launch_typed<__half, true>(a, s, es);
-        else launch_typed<__half, false>(a, s, es);
+        if (collision == 0) launch_typed<__half, true>(a, stats, s, es);
+        else launch_typed<__half, false>(a, stats, s, es);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (forked) {

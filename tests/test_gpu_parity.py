@@ -54,6 +54,11 @@ def test_single_step_channel(collision):
     ((33, 7, 11), dict(bc_x="periodic", force=(2e-5, -1e-5, 3e-6))),  # periodic x + walls + force
     ((16, 12, 10), dict(bc_x="periodic", bc_y="periodic", collision="bgk", force=(1e-5, 0.0, 2e-5))),
     ((70, 3, 17), dict(collision="bgk", t_filter=0.0)),
+    ((200, 6, 5), dict()),                                            # two-cells-per-thread interior
+    ((256, 4, 3), dict(bc_x="periodic", collision="bgk", force=(3e-5, 1e-5, -2e-5))),
+    ((258, 7, 2), dict(bc_x="periodic", bc_y="periodic", force=(1e-5, -3e-5, 0.0))),
+    ((101, 5, 7), dict()),                                            # odd nx: scalar interior kernel
+    ((131, 9, 1), dict(bc_x="periodic", force=(2e-5, 0.0, 0.0))),
 ])
 def test_single_step_ragged_and_variants(dims, kw):
     nx, ny, nz = dims
@@ -98,6 +103,25 @@ def test_200_steps_channel_velocity_and_statistics():
     assert abs(st["mass"] - fo.sum()) / fo.sum() < 1e-6
 
 
+@pytest.mark.parametrize("dims,storage", [((200, 8, 6), "fp32"), ((101, 5, 7), "fp32"), ((200, 8, 6), "fp16s")])
+def test_statistics_every_step_small(dims, storage):
+    """Sampling on every step through all kernels (pair, scalar, edge)."""
+    nx, ny, nz = dims
+    c = SMALL.with_(nx=nx, ny=ny, nz=nz, stats_every=1, storage=storage, n_modes=24)
+    gpu, orc = pair(c, check_every=1, mass_tol=0.5)
+    for n in (1, 3):
+        gpu.step(n)
+        orc.step(n)
+    st = gpu.stats()
+    assert st["rc"] == 0, st["error"]
+    m, r, n = orc.stats()
+    assert st["n_samples"] == n == 4
+    tol = 1e-4 if storage == "fp32" else 2e-3
+    assert normwise(st["mean_sum"], m) < tol
+    assert normwise(st["rey_sum"], r) < tol
+    assert abs(st["mass"] - orc.pops().sum()) / orc.pops().sum() < (1e-6 if storage == "fp32" else 1e-4)
+
+
 def test_mass_conservation_periodic_box_gpu():
     c = SMALL.with_(nx=32, ny=32, nz=32, bc_x="periodic", bc_y="periodic", stats_every=0)
     from paper_2205_02774_gb300.channel import Channel
@@ -126,8 +150,10 @@ def test_poiseuille_gpu(collision, lam):
     assert normwise(ux, exact) < 2e-4
 
 
-def test_fp16_single_step():
-    c = SMALL.with_(storage="fp16s", stats_every=0)
+@pytest.mark.parametrize("dims", [(64, 32, 32), (200, 6, 5), (101, 5, 7)])
+def test_fp16_single_step(dims):
+    nx, ny, nz = dims
+    c = SMALL.with_(storage="fp16s", stats_every=0, nx=nx, ny=ny, nz=nz)
     gpu, orc = pair(c)
     f = perturbed_equilibrium_field(c.nx, c.ny, c.nz, seed=4)
     bits = fp16_bits(f)
