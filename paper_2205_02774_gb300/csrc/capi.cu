@@ -598,6 +598,11 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
         rc = build_inlet(h, rans, seed);
         if (rc) return bail(rc);
     }
+    e = stg::tma_prepare();
+    if (e != cudaSuccess) {
+        cuda_fail(h, e, "tma_prepare");
+        return bail(STG_ERR_CUDA);
+    }
     e = stg::launch_init_equilibrium(h->lat[0], domain->storage, nx, ny, nz, h->inout ? h->u_int : nullptr,
                                      h->stream);
     if (e != cudaSuccess) {
@@ -707,6 +712,12 @@ int stg_lbm_stats(stg_lbm *h, stg_stats *out)
     const int64_t k = h->d.stats_every;
     out->n_samples = k > 0 ? (h->t / k - h->t0_stats / k) : 0;
     out->mass0 = h->mass0;
+    unsigned long long kerr = 0;
+    CK(cudaMemcpy(&kerr, &h->ctl->err, sizeof kerr, cudaMemcpyDeviceToHost));
+    if (kerr) {
+        h->sticky = STG_ERR_TIMEOUT;
+        return fail(h, STG_ERR_TIMEOUT, "a kernel's bounded wait for its staged copies expired");
+    }
     double mass = 0.0;
     int rc2 = compute_mass(h, &mass);
     if (rc2) return rc2;

@@ -14,7 +14,7 @@ namespace stg {
 struct StepCtl {
     long long t[2];
     long long t0_filter;  // step at which the temporal filter restarts
-    long long pad;
+    unsigned long long err; // error bits set by kernels (1: bounded wait on an mbarrier expired)
 };
 
 struct StepArgs {
@@ -86,6 +86,13 @@ cudaError_t launch_setup_nodes(int ny, int N, const double *R6, const double *le
 cudaError_t launch_init_equilibrium(void *dst, int storage, int nx, int ny, int nz, const float *u_int,
                                     cudaStream_t s);
 cudaError_t launch_mass(const MassArgs &a, cudaStream_t s);
+
+// TMA-staged interior kernel (tma_kernel.cu): usable when a lattice row is a
+// whole number of 16-byte units; tma_prepare() raises the kernels' dynamic
+// shared-memory limit (call once before launching or capturing).
+bool tma_usable(int nx, int storage);
+cudaError_t tma_prepare();
+cudaError_t launch_tma(const StepArgs &a, int gx, int gy, int storage, int collision, bool stats, cudaStream_t s);
 
 int step_grid_blocks(int nx, int ny);
 int mass_grid_blocks();

@@ -19,6 +19,7 @@
 #include "d3q19.cuh"
 #include "internal.h"
 #include "lbm_cell.cuh"
+#include "reduce.cuh"
 
 namespace stg {
 
@@ -61,46 +62,6 @@ __device__ __forceinline__ void gather_general(const S *__restrict__ src, unsign
         const unsigned pl = yw ? (unsigned)opp_of(i) : (unsigned)i;
         const unsigned c2 = yw ? here : cell;
         g[i] = (yw || xok) ? Pop<S>::ld(src + (size_t)pl * P + c2) : 0.0f;
-    }
-}
-
-// Deterministic FP64 mass of the pass: each block leaves its partial at
-// mass_partial[part] (and 0 at `zero` when it spans two 32-wide columns); the
-// last of all total_blocks blocks adds the nxc*ny partials in index order.
-__device__ __forceinline__ void mass_finish(const StepArgs &a, float sdr, int part, int zero)
-{
-    __shared__ double rd[BX * BZ];
-    __shared__ int s_last;
-    const int tid = threadIdx.y * BX + threadIdx.x;
-    rd[tid] = (double)sdr;
-    __syncthreads();
-    for (int off = BZ * BX / 2; off > 0; off >>= 1) {
-        if (tid < off) rd[tid] += rd[tid + off];
-        __syncthreads();
-    }
-    const unsigned nparts = (unsigned)((a.nx + BX - 1) / BX) * a.ny;
-    if (tid == 0) {
-        a.mass_partial[part] = rd[0];
-        if (zero >= 0) a.mass_partial[zero] = 0.0;
-        __threadfence();
-        const unsigned prev = atomicAdd(a.mass_counter, 1u);
-        s_last = (prev == a.total_blocks - 1);
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        double acc = 0.0;
-        for (unsigned k = tid; k < nparts; k += BZ * BX) acc += __ldcg(a.mass_partial + k);
-        rd[tid] = acc;
-        __syncthreads();
-        for (int off = BZ * BX / 2; off > 0; off >>= 1) {
-            if (tid < off) rd[tid] += rd[tid + off];
-            __syncthreads();
-        }
-        if (tid == 0) {
-            a.mass_out[0] = rd[0] + (double)a.P;
-            *a.mass_counter = 0u;
-        }
     }
 }
 
@@ -229,7 +190,7 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
             }
         }
     }
-    if (do_check) mass_finish(a, sdr, y * ((nx + BX - 1) / BX) + bx, -1);
+    if (do_check) mass_finish<BX * BZ>(a, sdr, y * ((nx + BX - 1) / BX) + bx, -1);
 }
 
 // Scalar interior columns: x chunks [il, ir), y = 1..ny-2 (odd nx or narrow lattices).
@@ -415,7 +376,7 @@ __global__ void __launch_bounds__(BX *BZ, 3) lbm_pair_kernel(const StepArgs a)
     }
     if (do_check) {
         const int nxc = (nx + BX - 1) / BX;
-        mass_finish(a, sdr, y * nxc + 2 * c, y * nxc + 2 * c + 1);
+        mass_finish<BX * BZ>(a, sdr, y * nxc + 2 * c, y * nxc + 2 * c + 1);
     }
 }
 
@@ -490,7 +451,10 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, cudaStream_t 
     lbm_edge_kernel<S, REG, FORCE><<<sp.n_edge, block, 0, side>>>(a);
     if (sp.gx > 0 && sp.gy > 0) {
         const dim3 grid(sp.gx, sp.gy);
-        if (sp.pair) {
+        const int storage = sizeof(S) == 4 ? 0 : 1;
+        if (sp.pair && tma_usable(a.nx, storage)) {
+            launch_tma(a, sp.gx, sp.gy, storage, REG ? 0 : 1, stats, s);
+        } else if (sp.pair) {
             if (stats) lbm_pair_kernel<S, REG, FORCE, true><<<grid, block, 0, s>>>(a);
             else lbm_pair_kernel<S, REG, FORCE, false><<<grid, block, 0, s>>>(a);
         } else {

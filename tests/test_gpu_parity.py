@@ -58,6 +58,7 @@ def test_single_step_channel(collision):
     ((256, 4, 3), dict(bc_x="periodic", collision="bgk", force=(3e-5, 1e-5, -2e-5))),
     ((258, 7, 2), dict(bc_x="periodic", bc_y="periodic", force=(1e-5, -3e-5, 0.0))),
     ((101, 5, 7), dict()),                                            # odd nx: scalar interior kernel
+    ((260, 5, 4), dict(collision="bgk")),                             # even nx, rows not 16 B: pair kernel
     ((131, 9, 1), dict(bc_x="periodic", force=(2e-5, 0.0, 0.0))),
 ])
 def test_single_step_ragged_and_variants(dims, kw):
@@ -103,7 +104,8 @@ def test_200_steps_channel_velocity_and_statistics():
     assert abs(st["mass"] - fo.sum()) / fo.sum() < 1e-6
 
 
-@pytest.mark.parametrize("dims,storage", [((200, 8, 6), "fp32"), ((101, 5, 7), "fp32"), ((200, 8, 6), "fp16s")])
+@pytest.mark.parametrize("dims,storage", [((200, 8, 6), "fp32"), ((101, 5, 7), "fp32"), ((200, 8, 6), "fp16s"),
+                                          ((258, 8, 6), "fp32"), ((260, 6, 5), "fp16s")])
 def test_statistics_every_step_small(dims, storage):
     """Sampling on every step through all kernels (pair, scalar, edge)."""
     nx, ny, nz = dims
@@ -150,7 +152,7 @@ def test_poiseuille_gpu(collision, lam):
     assert normwise(ux, exact) < 2e-4
 
 
-@pytest.mark.parametrize("dims", [(64, 32, 32), (200, 6, 5), (101, 5, 7)])
+@pytest.mark.parametrize("dims", [(64, 32, 32), (200, 6, 5), (101, 5, 7), (260, 5, 4)])
 def test_fp16_single_step(dims):
     nx, ny, nz = dims
     c = SMALL.with_(storage="fp16s", stats_every=0, nx=nx, ny=ny, nz=nz)
