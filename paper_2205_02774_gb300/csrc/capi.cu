@@ -51,6 +51,8 @@ struct stg_lbm {
     double *h_pinned = nullptr;  // [0]: last checked mass
     cudaEvent_t ev_check = nullptr, ev_done = nullptr;
     cudaStream_t side = nullptr;                       // branch for the edge kernel
+    alignas(64) unsigned char tmap[2][128];            // tensor maps of the two lattices (CUtensorMap)
+    bool has_tmap = false;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool check_pending = false;
     int64_t t = 0, t0_stats = 0;
@@ -355,8 +357,8 @@ cudaError_t enqueue_step(stg_lbm *h, int parity, bool stats)
         e = stg::launch_inlet(inlet_args(h, parity), h->stream);
         if (e != cudaSuccess) return e;
     }
-    return stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, stats, h->stream, h->side,
-                            h->ev_fork, h->ev_join);
+    return stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, stats,
+                            h->has_tmap ? h->tmap[parity] : nullptr, h->stream, h->side, h->ev_fork, h->ev_join);
 }
 
 // Graph of `steps` steps starting with parity p0.  single_stats >= 0: one
@@ -603,6 +605,10 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
         cuda_fail(h, e, "tma_prepare");
         return bail(STG_ERR_CUDA);
     }
+    if (stg::tma_usable(nx, domain->storage)) {
+        h->has_tmap = stg::tma_encode(h->tmap[0], h->lat[0], domain->storage, nx, ny, nz) == 0 &&
+                      stg::tma_encode(h->tmap[1], h->lat[1], domain->storage, nx, ny, nz) == 0;
+    }
     e = stg::launch_init_equilibrium(h->lat[0], domain->storage, nx, ny, nz, h->inout ? h->u_int : nullptr,
                                      h->stream);
     if (e != cudaSuccess) {
@@ -675,7 +681,8 @@ int stg_lbm_step_timed(stg_lbm *h, int64_t n, double *ms_step, double *ms_inlet)
         if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], h->stream);
         if (e == cudaSuccess)
             e = stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, is_stats_step(h, h->t),
-                                 h->stream, h->side, h->ev_fork, h->ev_join);
+                                 h->has_tmap ? h->tmap[parity] : nullptr, h->stream, h->side, h->ev_fork,
+                                 h->ev_join);
         if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], h->stream);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "timed step launch");
         else h->t += 1;

@@ -77,8 +77,9 @@ struct MassArgs {
 // launchers (return the launch status)
 // `stats` must be true exactly on sampling steps ((t + 1) % stats_every == 0);
 // the host tracks t and decides.
-cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, cudaStream_t s,
-                        cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
+// tensor_map: the source lattice's tensor map (nullptr: no TMA-staged kernel)
+cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, const void *tensor_map,
+                        cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 cudaError_t launch_inlet(const InletArgs &a, cudaStream_t s);
 cudaError_t launch_setup_nodes(int ny, int N, const double *R6, const double *le, const double *leta,
                                const double *lcut, const double *kn, const double *dk, float *a6,
@@ -92,7 +93,11 @@ cudaError_t launch_mass(const MassArgs &a, cudaStream_t s);
 // shared-memory limit (call once before launching or capturing).
 bool tma_usable(int nx, int storage);
 cudaError_t tma_prepare();
-cudaError_t launch_tma(const StepArgs &a, int gx, int gy, int storage, int collision, bool stats, cudaStream_t s);
+// encode the tensor map of one stored lattice into map_out (a 64-byte aligned
+// CUtensorMap); 0 on success
+int tma_encode(void *map_out, const void *lattice, int storage, int nx, int ny, int nz);
+cudaError_t launch_tma(const StepArgs &a, const void *tensor_map, int gx, int gy, int storage, int collision,
+                       bool stats, cudaStream_t s);
 
 int step_grid_blocks(int nx, int ny);
 int mass_grid_blocks();

@@ -445,15 +445,16 @@ static Split split_of(int nx, int ny, int nz)
 }
 
 template <typename S, bool REG, bool FORCE>
-static void launch_forced(StepArgs a, const Split &sp, bool stats, cudaStream_t s, cudaStream_t side)
+static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *tmap, cudaStream_t s,
+                          cudaStream_t side)
 {
     const dim3 block(BX, BZ);
     lbm_edge_kernel<S, REG, FORCE><<<sp.n_edge, block, 0, side>>>(a);
     if (sp.gx > 0 && sp.gy > 0) {
         const dim3 grid(sp.gx, sp.gy);
         const int storage = sizeof(S) == 4 ? 0 : 1;
-        if (sp.pair && tma_usable(a.nx, storage)) {
-            launch_tma(a, sp.gx, sp.gy, storage, REG ? 0 : 1, stats, s);
+        if (sp.pair && tmap && tma_usable(a.nx, storage)) {
+            launch_tma(a, tmap, sp.gx, sp.gy, storage, REG ? 0 : 1, stats, s);
         } else if (sp.pair) {
             if (stats) lbm_pair_kernel<S, REG, FORCE, true><<<grid, block, 0, s>>>(a);
             else lbm_pair_kernel<S, REG, FORCE, false><<<grid, block, 0, s>>>(a);
@@ -464,22 +465,22 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, cudaStream_t 
 }
 
 template <typename S, bool REG>
-static void launch_typed(const StepArgs &a0, bool stats, cudaStream_t s, cudaStream_t side)
+static void launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaStream_t s, cudaStream_t side)
 {
     const Split sp = split_of(a0.nx, a0.ny, a0.nz);
     StepArgs a = a0;
     a.il = sp.il;
     a.ir = sp.ir;
     a.total_blocks = (unsigned)(sp.n_edge + sp.gx * sp.gy);
-    if (a.has_force) launch_forced<S, REG, true>(a, sp, stats, s, side);
-    else launch_forced<S, REG, false>(a, sp, stats, s, side);
+    if (a.has_force) launch_forced<S, REG, true>(a, sp, stats, tmap, s, side);
+    else launch_forced<S, REG, false>(a, sp, stats, tmap, s, side);
 }
 
 // One fused step pass.  With a side stream and two events the edge columns
 // run on a forked branch concurrently with the interior columns (both read
 // only the previous lattice and write disjoint cells); `s` waits for both.
-cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, cudaStream_t s,
-                        cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
+cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, const void *tmap,
+                        cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
 {
     cudaError_t e = cudaSuccess;
     const bool forked = side != nullptr && fork != nullptr && join != nullptr;
@@ -489,11 +490,11 @@ cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stat
     }
     cudaStream_t es = forked ? side : s;
     if (storage == 0) {
-        if (collision == 0) launch_typed<float, true>(a, stats, s, es);
-        else launch_typed<float, false>(a, stats, s, es);
+        if (collision == 0) launch_typed<float, true>(a, stats, tmap, s, es);
+        else launch_typed<float, false>(a, stats, tmap, s, es);
     } else {
-        if (collision == 0) launch_typed<__half, true>(a, stats, s, es);
-        else launch_typed<__half, false>(a, stats, s, es);
+        if (collision == 0) launch_typed<__half, true>(a, stats, tmap, s, es);
+        else launch_typed<__half, false>(a, stats, tmap, s, es);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (forked) {

@@ -58,6 +58,8 @@ CASES = {
                                        n_modes=200, n_fv=96, steps=20000),
     # mid-size channel (h = 32) used for detailed profiles: 2.4M cells, lattice > L2
     "channel_384x64x96": ChannelCase("channel_384x64x96", 384, 64, 96, n_modes=200, n_fv=96, steps=2000),
+    # production cross-section rows (768 x 128) with a shallow span, for detailed profiles: 4.7M cells
+    "channel_768x128x48": ChannelCase("channel_768x128x48", 768, 128, 48, n_modes=200, n_fv=96, steps=2000),
     # refined channel: h = 128, 151M cells
     "channel_1536x256x384": ChannelCase("channel_1536x256x384", 1536, 256, 384,
                                         n_modes=200, n_fv=96, steps=20000),
