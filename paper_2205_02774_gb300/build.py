@@ -20,6 +20,11 @@ SOURCES = ["capi.cu", "step_kernel.cu", "inlet_kernel.cu", "tma_kernel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE,
               "--expt-relaxed-constexpr"]
+# The FP32 step arithmetic uses the hardware approximate reciprocal and square
+# root (a few ulp, far inside the parity tolerance) and flushes denormals; the
+# FP64 setup code is unaffected by these flags.
+FAST_FP32 = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+FAST_TUS = {"step_kernel.cu", "tma_kernel.cu"}
 
 
 def _nvcc():
@@ -43,7 +48,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        fast = FAST_FP32 if src in FAST_TUS else []
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *fast, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <thread>
@@ -66,6 +67,7 @@ struct stg_lbm {
     int block_steps = 16;
     stg_info info{};
     double timeout_s = 900.0;
+    int interior = 0;  // STG_LBM_INTERIOR=scalar|pair|tma overrides the interior kernel choice
 };
 
 namespace {
@@ -312,6 +314,7 @@ stg::StepArgs step_args(const stg_lbm *h, int parity)
     a.ctl = h->ctl;
     a.parity = parity;
     a.stats_every = h->d.stats_every;
+    a.interior = h->interior;
     a.check_every = h->d.check_every;
     a.stat_mean = h->stat_mean;
     a.stat_rey = h->stat_rey;
@@ -566,6 +569,10 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
         return bail(STG_ERR_CUDA);
     }
     const int nx = domain->nx, ny = domain->ny, nz = domain->nz;
+    if (const char *ev = std::getenv("STG_LBM_INTERIOR")) {
+        const std::string v(ev);
+        h->interior = v == "scalar" ? 1 : v == "pair" ? 2 : v == "tma" ? 3 : 0;
+    }
     h->P = (size_t)nx * ny * nz;
     h->elem = domain->storage == STG_FP32 ? 4 : 2;
     h->lat[0] = dalloc(h, 19 * h->P * h->elem);

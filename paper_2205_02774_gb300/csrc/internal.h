@@ -30,6 +30,7 @@ struct StepArgs {
     const void *srcy[19];
     void *dstp[19];
     int il, ir;             // 32-wide x chunks [il, ir) of rows 1..ny-2 belong to the interior kernel
+    int interior;           // interior kernel: 0 best available, 1 one cell per thread, 2 cell pairs, 3 TMA-staged
     unsigned total_blocks;  // blocks of all step kernels of the pass (mass-check completion count)
     int nx, ny, nz;
     unsigned P;           // cells per population plane (nx*ny*nz)

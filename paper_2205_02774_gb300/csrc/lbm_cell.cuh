@@ -79,10 +79,21 @@ __device__ __forceinline__ void rebuild(float (&g)[Q], float drho, float ux, flo
 }
 
 // Moments, Smagorinsky relaxation and collision of one cell, in shifted
-// variables, written over opposite pairs (i, i+1), c_{i+1} = -c_i: every
-// term of the update is either even in c (equilibrium second order,
-// regularized non-equilibrium, force x velocity) or odd (first order), so
-// each pair costs one even and one odd part.
+// variables.  Both collisions are written as
+//     g*_i = K g_i + w_i [a0 + c_i.B + c_i.A.c_i]
+// with K = 0 for the regularized collision (eq. f_i_neq applied in the bulk)
+// and K = 1 - 1/tau for plain BGK (eq. lbe); the scalar a0, vector B and
+// symmetric tensor A gather the shifted equilibrium (eq. local_eq), the
+// regularized non-equilibrium part and the Guo force term (eq. bodyforce):
+//   regularized: a0 = drho - 1.5 rho u.u - 1.5 (1-w) tr Pi_neq - 3 kf u.F
+//                B  = 3 rho u + (3 kf - 1.5 (1-w)) F
+//                A  = 4.5 rho u u + 4.5 (1-w) Pi_neq + 9 kf sym(u F)
+//   BGK:         a0 = w (drho - 1.5 rho u.u) - 3 kf u.F
+//                B  = 3 w rho u + 3 kf F
+//                A  = 4.5 w rho u u + 9 kf sym(u F)
+// (w = 1/tau_eff here, kf = 1 - w/2).  The 18 moving populations come in
+// opposite pairs, and the edge pairs (a, b, +-) share A_aa + A_bb, so the
+// whole update is a few dozen fused multiply-adds.
 template <bool REG, bool FORCE>
 __device__ __forceinline__ void collide(float (&g)[Q], float tau0, float kq, float Fx, float Fy, float Fz,
                                         float &rho_o, float &ux_o, float &uy_o, float &uz_o)
@@ -93,6 +104,8 @@ __device__ __forceinline__ void collide(float (&g)[Q], float tau0, float kq, flo
         s[p] = g[2 * p + 1] + g[2 * p + 2];
         d[p] = g[2 * p + 1] - g[2 * p + 2];
     }
+    // moments, eqs. (density), (momentum), (tensor): rho = 1 + sum g,
+    // rho u = sum c g (+ F/2), Pi = sum c c g + I/3
     float drho = g[0], jx = 0.f, jy = 0.f, jz = 0.f;
     float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
 #pragma unroll
@@ -117,72 +130,114 @@ __device__ __forceinline__ void collide(float (&g)[Q], float tau0, float kq, flo
     const float uz = (FORCE ? jz + 0.5f * Fz : jz) * irho;
     // Pi_neq = Pi - rho (cs^2 I + u u) = sum c c g - drho/3 I - rho u u
     const float rux = rho * ux, ruy = rho * uy, ruz = rho * uz;
-    const float nxx = pxx - drho * (1.0f / 3.0f) - rux * ux;
-    const float nyy = pyy - drho * (1.0f / 3.0f) - ruy * uy;
-    const float nzz = pzz - drho * (1.0f / 3.0f) - ruz * uz;
+    const float d3 = drho * (1.0f / 3.0f);
+    const float nxx = pxx - d3 - rux * ux;
+    const float nyy = pyy - d3 - ruy * uy;
+    const float nzz = pzz - d3 - ruz * uz;
     const float nxy = pxy - rux * uy;
     const float nxz = pxz - rux * uz;
     const float nyz = pyz - ruy * uz;
-    const float qh = sqrtf(nxx * nxx + nyy * nyy + nzz * nzz + 2.0f * (nxy * nxy + nxz * nxz + nyz * nyz));
+    const float q2 = nxx * nxx + nyy * nyy + nzz * nzz + 2.0f * (nxy * nxy + nxz * nxz + nyz * nyz);
+    const float qh = q2 > 0.f ? sqrtf(q2) : 0.f;
     // eq. (tau_eff), c = 1: tau = tau0/2 + sqrt((tau0 rho)^2 + 18 sqrt2 C Q^1/2)/(2 rho)
-    const float tau = 0.5f * tau0 + 0.5f * sqrtf(tau0 * tau0 + kq * qh * irho * irho);
+    const float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + kq * qh * irho * irho));
     const float om = 1.0f / tau;
     const float uu = ux * ux + uy * uy + uz * uz;
-    const float tr3 = (nxx + nyy + nzz) * (1.0f / 3.0f);
+    const float kf = FORCE ? (1.0f - 0.5f * om) : 0.f;  // Guo prefactor
     const float uF = FORCE ? ux * Fx + uy * Fy + uz * Fz : 0.f;
-    const float kneq = REG ? 4.5f * (1.0f - om) : 0.f;   // (1 - 1/tau) w_i/(2 cs^4) / w_i
-    const float kf = FORCE ? (1.0f - 0.5f * om) : 0.f;   // Guo prefactor
-    // base of the even part shared by all directions: drho - 1.5 rho u.u
-    const float e0 = drho - 1.5f * rho * uu;
-    // rest population
-    {
-        const float w = w_of(0);
-        float ge = w * e0;
-        if (REG) {
-            float go = ge - w * kneq * tr3;
-            if (FORCE) go += kf * w * (-3.0f * uF);
-            g[0] = go;
-        } else {
-            float go = g[0] - om * (g[0] - ge);
-            if (FORCE) go += kf * w * (-3.0f * uF);
-            g[0] = go;
+    float a0, Bx, By, Bz, Axx, Ayy, Azz, Axy, Axz, Ayz, K;
+    if (REG) {
+        const float km = 1.0f - om;
+        const float k45 = 4.5f * km;
+        a0 = drho - 1.5f * rho * uu - 1.5f * km * (nxx + nyy + nzz);
+        Bx = 3.0f * rux;
+        By = 3.0f * ruy;
+        Bz = 3.0f * ruz;
+        Axx = 4.5f * rux * ux + k45 * nxx;
+        Ayy = 4.5f * ruy * uy + k45 * nyy;
+        Azz = 4.5f * ruz * uz + k45 * nzz;
+        Axy = 4.5f * rux * uy + k45 * nxy;
+        Axz = 4.5f * rux * uz + k45 * nxz;
+        Ayz = 4.5f * ruy * uz + k45 * nyz;
+        K = 0.f;
+        if (FORCE) {
+            // regularized: the first-order neq part a1 = -F/2 is kept
+            const float kb = 3.0f * kf - 1.5f * km;
+            Bx += kb * Fx;
+            By += kb * Fy;
+            Bz += kb * Fz;
+        }
+    } else {
+        a0 = om * (drho - 1.5f * rho * uu);
+        const float r3 = 3.0f * om, r45 = 4.5f * om;
+        Bx = r3 * rux;
+        By = r3 * ruy;
+        Bz = r3 * ruz;
+        Axx = r45 * rux * ux;
+        Ayy = r45 * ruy * uy;
+        Azz = r45 * ruz * uz;
+        Axy = r45 * rux * uy;
+        Axz = r45 * rux * uz;
+        Ayz = r45 * ruy * uz;
+        K = 1.0f - om;
+        if (FORCE) {
+            Bx += 3.0f * kf * Fx;
+            By += 3.0f * kf * Fy;
+            Bz += 3.0f * kf * Fz;
         }
     }
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-        const int i = 2 * p + 1;
-        const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const float w = w_of(i);
-        const float cu = cx * ux + cy * uy + cz * uz;
-        // even and odd parts of the shifted equilibrium: w [e0 + 4.5 rho cu^2] +- w 3 rho cu
-        float ev = w * (e0 + 4.5f * rho * cu * cu);
-        float od = w * 3.0f * rho * cu;
+    if (FORCE) {
+        const float k9 = 9.0f * kf;
+        a0 -= 3.0f * kf * uF;
+        Axx += k9 * ux * Fx;
+        Ayy += k9 * uy * Fy;
+        Azz += k9 * uz * Fz;
+        Axy += 0.5f * k9 * (ux * Fy + uy * Fx);
+        Axz += 0.5f * k9 * (ux * Fz + uz * Fx);
+        Ayz += 0.5f * k9 * (uy * Fz + uz * Fy);
+    }
+    constexpr float W0 = 1.0f / 3.0f, W1 = 1.0f / 18.0f, W2 = 1.0f / 36.0f;
+    // rest population
+    g[0] = REG ? W0 * a0 : fmaf(K, g[0], W0 * a0);
+    // axis pairs (1,2) +-x, (3,4) +-y, (5,6) +-z
+    {
+        const float w1a0 = W1 * a0;
+        const float ex = fmaf(W1, Axx, w1a0), ey = fmaf(W1, Ayy, w1a0), ez = fmaf(W1, Azz, w1a0);
+        const float ox = W1 * Bx, oy = W1 * By, oz = W1 * Bz;
         if (REG) {
-            const float cpc = cx * cx * nxx + cy * cy * nyy + cz * cz * nzz
-                            + 2.0f * (cx * cy * nxy + cx * cz * nxz + cy * cz * nyz);
-            ev += w * kneq * (cpc - tr3);
-        }
-        if (FORCE) {
-            const float cF = cx * Fx + cy * Fy + cz * Fz;
-            // Guo term, eq. (bodyforce): even part 9 (c.u)(c.F) - 3 u.F, odd part 3 c.F
-            ev += kf * w * (9.0f * cu * cF - 3.0f * uF);
-            od += kf * w * 3.0f * cF;
-            // regularized: keep the first-order neq part a1 = -F/2
-            if (REG) od -= (1.0f - om) * 1.5f * w * cF;
-        }
-        if (REG) {
-            g[i] = ev + od;
-            g[i + 1] = ev - od;
+            g[1] = ex + ox; g[2] = ex - ox;
+            g[3] = ey + oy; g[4] = ey - oy;
+            g[5] = ez + oz; g[6] = ez - oz;
         } else {
-            g[i] = g[i] - om * (g[i] - (ev + od));
-            g[i + 1] = g[i + 1] - om * (g[i + 1] - (ev - od));
-            if (FORCE) {
-                // the Guo parts were folded into ev/od above; undo the relaxation on them
-                const float cF = cx * Fx + cy * Fy + cz * Fz;
-                const float fe = kf * w * (9.0f * cu * cF - 3.0f * uF), fo = kf * w * 3.0f * cF;
-                g[i] += (1.0f - om) * (fe + fo);
-                g[i + 1] += (1.0f - om) * (fe - fo);
-            }
+            g[1] = fmaf(K, g[1], ex + ox); g[2] = fmaf(K, g[2], ex - ox);
+            g[3] = fmaf(K, g[3], ey + oy); g[4] = fmaf(K, g[4], ey - oy);
+            g[5] = fmaf(K, g[5], ez + oz); g[6] = fmaf(K, g[6], ez - oz);
+        }
+    }
+    // edge pairs: (7,8) +-(1,1,0), (9,10) +-(1,-1,0), (11,12) +-(1,0,1), (13,14) +-(1,0,-1),
+    //             (15,16) +-(0,1,1), (17,18) +-(0,1,-1)
+    {
+        const float w2a0 = W2 * a0;
+        const float bx = W2 * Bx, by = W2 * By, bz = W2 * Bz;
+        const float sxy = fmaf(W2, Axx + Ayy, w2a0), txy = (2.0f * W2) * Axy;
+        const float sxz = fmaf(W2, Axx + Azz, w2a0), txz = (2.0f * W2) * Axz;
+        const float syz = fmaf(W2, Ayy + Azz, w2a0), tyz = (2.0f * W2) * Ayz;
+        const float e7 = sxy + txy, e9 = sxy - txy, e11 = sxz + txz, e13 = sxz - txz, e15 = syz + tyz, e17 = syz - tyz;
+        const float o7 = bx + by, o9 = bx - by, o11 = bx + bz, o13 = bx - bz, o15 = by + bz, o17 = by - bz;
+        if (REG) {
+            g[7] = e7 + o7; g[8] = e7 - o7;
+            g[9] = e9 + o9; g[10] = e9 - o9;
+            g[11] = e11 + o11; g[12] = e11 - o11;
+            g[13] = e13 + o13; g[14] = e13 - o13;
+            g[15] = e15 + o15; g[16] = e15 - o15;
+            g[17] = e17 + o17; g[18] = e17 - o17;
+        } else {
+            g[7] = fmaf(K, g[7], e7 + o7); g[8] = fmaf(K, g[8], e7 - o7);
+            g[9] = fmaf(K, g[9], e9 + o9); g[10] = fmaf(K, g[10], e9 - o9);
+            g[11] = fmaf(K, g[11], e11 + o11); g[12] = fmaf(K, g[12], e11 - o11);
+            g[13] = fmaf(K, g[13], e13 + o13); g[14] = fmaf(K, g[14], e13 - o13);
+            g[15] = fmaf(K, g[15], e15 + o15); g[16] = fmaf(K, g[16], e15 - o15);
+            g[17] = fmaf(K, g[17], e17 + o17); g[18] = fmaf(K, g[18], e17 - o17);
         }
     }
     rho_o = rho;

@@ -416,12 +416,12 @@ struct Split {
     int n_edge;
 };
 
-static Split split_of(int nx, int ny, int nz)
+static Split split_of(int nx, int ny, int nz, int interior)
 {
     Split sp{};
     const int nxc = (nx + BX - 1) / BX;
     const int C = nx / 64;
-    sp.pair = (nx % 2 == 0) && C >= 3 && ny >= 3 && 19.0 * nx * ny * nz < 4294967296.0;
+    sp.pair = interior != 1 && (nx % 2 == 0) && C >= 3 && ny >= 3 && 19.0 * nx * ny * nz < 4294967296.0;
     if (sp.pair) {
         sp.il = 2;
         sp.ir = 2 * (C - 1);
@@ -453,7 +453,7 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
     if (sp.gx > 0 && sp.gy > 0) {
         const dim3 grid(sp.gx, sp.gy);
         const int storage = sizeof(S) == 4 ? 0 : 1;
-        if (sp.pair && tmap && tma_usable(a.nx, storage)) {
+        if (sp.pair && tmap && a.interior != 2 && tma_usable(a.nx, storage)) {
             launch_tma(a, tmap, sp.gx, sp.gy, storage, REG ? 0 : 1, stats, s);
         } else if (sp.pair) {
             if (stats) lbm_pair_kernel<S, REG, FORCE, true><<<grid, block, 0, s>>>(a);
@@ -467,7 +467,7 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
 template <typename S, bool REG>
 static void launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaStream_t s, cudaStream_t side)
 {
-    const Split sp = split_of(a0.nx, a0.ny, a0.nz);
+    const Split sp = split_of(a0.nx, a0.ny, a0.nz, a0.interior);
     StepArgs a = a0;
     a.il = sp.il;
     a.ir = sp.ir;
