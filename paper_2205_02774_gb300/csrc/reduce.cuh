@@ -6,12 +6,12 @@
 namespace stg {
 
 // Deterministic FP64 mass of a step pass: each block leaves the sum of its
-// threads' (rho - 1) at mass_partial[part] (and 0 at `zero` when it spans two
-// 32-wide columns); the last of all total_blocks blocks adds the
-// ceil(nx/32) * ny partials in index order and writes nx ny nz + sum.
+// threads' (rho - 1) at mass_partial[part] and 0 in the slots [zb, ze) of the
+// other 32-wide columns it covers; the last of all total_blocks blocks adds
+// the ceil(nx/32) * ny partials in index order and writes nx ny nz + sum.
 // NT = threads per block (a power of two, at most 256).
 template <int NT>
-__device__ __forceinline__ void mass_finish(const StepArgs &a, float sdr, int part, int zero)
+__device__ __forceinline__ void mass_finish(const StepArgs &a, float sdr, int part, int zb, int ze)
 {
     __shared__ double rd[NT];
     __shared__ int s_last;
@@ -25,7 +25,7 @@ __device__ __forceinline__ void mass_finish(const StepArgs &a, float sdr, int pa
     const unsigned nparts = (unsigned)((a.nx + 31) / 32) * a.ny;
     if (tid == 0) {
         a.mass_partial[part] = rd[0];
-        if (zero >= 0) a.mass_partial[zero] = 0.0;
+        for (int k = zb; k < ze; ++k) a.mass_partial[k] = 0.0;
         __threadfence();
         const unsigned prev = atomicAdd(a.mass_counter, 1u);
         s_last = (prev == a.total_blocks - 1);

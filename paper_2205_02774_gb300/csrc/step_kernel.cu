@@ -190,7 +190,7 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
             }
         }
     }
-    if (do_check) mass_finish<BX * BZ>(a, sdr, y * ((nx + BX - 1) / BX) + bx, -1);
+    if (do_check) mass_finish<BX * BZ>(a, sdr, y * ((nx + BX - 1) / BX) + bx, 0, 0);
 }
 
 // Scalar interior columns: x chunks [il, ir), y = 1..ny-2 (odd nx or narrow lattices).
@@ -201,94 +201,106 @@ __global__ void __launch_bounds__(BX *BZ, 4) lbm_step_kernel(const StepArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Two cells per thread: lane l of a warp owns cells (x, x+1), x = 64 c + 2 l,
-// so every population row is read and written as aligned 8-byte (FP32) or
-// 4-byte (FP16) pairs, 256 B / 128 B per warp instruction.  A pull with
-// c_x = +1 needs (x-1, x): the x-1 value is the upper half of the left lane's
-// pair (warp shuffle), lane 0 reads it directly; c_x = -1 mirrors this.
-template <typename S>
-struct Pair;
+// Several cells per lane: lane l of a warp owns CPL consecutive cells starting
+// at x = x0 + CPL l, so every population row is read and written as aligned
+// vectors (FP32: 2 cells, 8 B; FP16: 4 cells, 8 B), 256 B per warp
+// instruction.  A pull with c_x = +1 needs the cells shifted by one: the
+// missing x-1 value is the top cell of the left lane's vector (warp shuffle;
+// lane 0 reads it directly), and c_x = -1 mirrors this on the right (the last
+// active lane reads it directly).  The wide accesses keep enough bytes in
+// flight per SM to saturate HBM, which 2-byte accesses cannot.
+template <typename S, int CPL>
+struct Vec;
 
 template <>
-struct Pair<float> {
+struct Vec<float, 2> {
     using raw = float2;
     static __device__ __forceinline__ raw ld(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
-    static __device__ __forceinline__ float lo(raw v) { return v.x; }
-    static __device__ __forceinline__ float hi(raw v) { return v.y; }
-    // (x-1, x) from the left lane's pair (x-2, x-1) and ours (x, x+1)
-    static __device__ __forceinline__ raw shift_in_left(raw cur, const float *p_xm1, int lane)
+    static __device__ __forceinline__ float cell(raw v, int j) { return j ? v.y : v.x; }
+    static __device__ __forceinline__ void put(raw &v, int j, float f)
+    {
+        if (j) v.y = f;
+        else v.x = f;
+    }
+    static __device__ __forceinline__ void st(float *p, raw v) { __stcs(reinterpret_cast<float2 *>(p), v); }
+    // (x-1, x) from the left lane's (x-2, x-1) and ours (x, x+1)
+    static __device__ __forceinline__ raw shift_left(raw cur, const float *p, bool side)
     {
         float l = __shfl_up_sync(0xffffffffu, cur.y, 1);
-        if (lane == 0) l = __ldg(p_xm1);
+        if (side) l = __ldg(p - 1);
         return make_float2(l, cur.x);
     }
-    // (x+1, x+2) from ours (x, x+1) and the right lane's (x+2, x+3)
-    static __device__ __forceinline__ raw shift_in_right(raw cur, const float *p_xp2, int lane)
+    // (x+1, x+2) from ours and the right lane's (x+2, x+3)
+    static __device__ __forceinline__ raw shift_right(raw cur, const float *p, bool side)
     {
         float r = __shfl_down_sync(0xffffffffu, cur.x, 1);
-        if (lane == 31) r = __ldg(p_xp2);
+        if (side) r = __ldg(p + 2);
         return make_float2(cur.y, r);
     }
-    static __device__ __forceinline__ void st(float *p, float a, float b)
-    {
-        __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
-    }
 };
+
+__device__ __forceinline__ float h2f(unsigned v, int hi) { return __half2float(__ushort_as_half((unsigned short)(hi ? v >> 16 : v & 0xffffu))); }
+__device__ __forceinline__ unsigned f2h(float f) { return (unsigned)__half_as_ushort(__float2half_rn(f)); }
 
 template <>
-struct Pair<__half> {
-    using raw = unsigned;  // two binary16: low half = x, high half = x+1
-    static __device__ __forceinline__ raw ld(const __half *p) { return __ldg(reinterpret_cast<const unsigned *>(p)); }
-    static __device__ __forceinline__ float lo(raw v) { return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu))); }
-    static __device__ __forceinline__ float hi(raw v) { return __half2float(__ushort_as_half((unsigned short)(v >> 16))); }
-    static __device__ __forceinline__ raw shift_in_left(raw cur, const __half *p_xm1, int lane)
+struct Vec<__half, 4> {
+    using raw = uint2;  // x: cells 0,1 (low half first); y: cells 2,3
+    static __device__ __forceinline__ raw ld(const __half *p) { return __ldg(reinterpret_cast<const uint2 *>(p)); }
+    static __device__ __forceinline__ float cell(raw v, int j) { return h2f(j < 2 ? v.x : v.y, j & 1); }
+    static __device__ __forceinline__ void put(raw &v, int j, float f)
     {
-        unsigned l = __shfl_up_sync(0xffffffffu, cur, 1);
-        if (lane == 0) l = (unsigned)__half_as_ushort(__ldg(p_xm1)) << 16;
-        return __byte_perm(l, cur, 0x5432);
+        unsigned &w = j < 2 ? v.x : v.y;
+        w = (j & 1) ? ((w & 0xffffu) | (f2h(f) << 16)) : ((w & 0xffff0000u) | f2h(f));
     }
-    static __device__ __forceinline__ raw shift_in_right(raw cur, const __half *p_xp2, int lane)
+    static __device__ __forceinline__ void st(__half *p, raw v) { __stcs(reinterpret_cast<uint2 *>(p), v); }
+    // (x-1, x, x+1, x+2)
+    static __device__ __forceinline__ raw shift_left(raw cur, const __half *p, bool side)
     {
-        unsigned r = __shfl_down_sync(0xffffffffu, cur, 1);
-        if (lane == 31) r = (unsigned)__half_as_ushort(__ldg(p_xp2));
-        return __byte_perm(cur, r, 0x5432);
+        unsigned l = __shfl_up_sync(0xffffffffu, cur.y, 1);
+        if (side) l = (unsigned)__half_as_ushort(__ldg(p - 1)) << 16;
+        return make_uint2(__byte_perm(l, cur.x, 0x5432), __byte_perm(cur.x, cur.y, 0x5432));
     }
-    static __device__ __forceinline__ void st(__half *p, float a, float b)
+    // (x+1, x+2, x+3, x+4)
+    static __device__ __forceinline__ raw shift_right(raw cur, const __half *p, bool side)
     {
-        const unsigned v = (unsigned)__half_as_ushort(__float2half_rn(a)) |
-                           ((unsigned)__half_as_ushort(__float2half_rn(b)) << 16);
-        __stcs(reinterpret_cast<unsigned *>(p), v);
+        unsigned r = __shfl_down_sync(0xffffffffu, cur.x, 1);
+        if (side) r = (unsigned)__half_as_ushort(__ldg(p + 4));
+        return make_uint2(__byte_perm(cur.x, cur.y, 0x5432), __byte_perm(cur.y, r, 0x5432));
     }
 };
 
-// write a result into the first cell of a raw pair / read it back
-__device__ __forceinline__ float2 pack_lo(float2 v, float a) { return make_float2(a, v.y); }
-__device__ __forceinline__ float lo_of(float2 v) { return v.x; }
-// FP16: the low half keeps the already rounded binary16 of the first cell's result
-__device__ __forceinline__ unsigned pack_lo(unsigned v, float a)
-{
-    return (v & 0xffff0000u) | (unsigned)__half_as_ushort(__float2half_rn(a));
-}
-__device__ __forceinline__ float lo_of(unsigned v) { return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu))); }
+template <typename S>
+struct VecOf {
+    static constexpr int CPL = 2;
+};
+template <>
+struct VecOf<__half> {
+    static constexpr int CPL = 4;
+};
 
-// z loop of one pair column; STATS adds the per-cell velocity sums to the
-// block's shared-memory slots (sampling steps only).  Returns the thread's
-// sum of rho - 1 when CHECK.
+// z loop of one vector column: x0 is the warp's first cell, x_end one past
+// the interior's last cell.  STATS adds the per-cell velocity sums to the
+// block's shared-memory slots.  Returns the thread's sum of rho - 1.
 template <typename S, bool REG, bool FORCE, bool STATS>
-__device__ __forceinline__ float pair_loop(const StepArgs &a, float (*sacc)[9][2 * BX], int c, int y)
+__device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX * VecOf<S>::CPL], int x0, int x_end,
+                                          int y)
 {
-    using PR = Pair<S>;
-    using raw = typename PR::raw;
+    constexpr int CPL = VecOf<S>::CPL;
+    using V = Vec<S, CPL>;
+    using raw = typename V::raw;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int nxy = nx * ny;
-    const int lane = threadIdx.x, tz = threadIdx.y;
-    const int x = 64 * c + 2 * lane;
+    const int lane = threadIdx.x, wi = threadIdx.y;
+    const int x = x0 + CPL * lane;
+    const bool active = x < x_end;
+    const bool side_l = lane == 0;
+    const bool side_r = lane == 31 || x + CPL == x_end;
     const float tau0 = a.tau0, kq = a.kq;
     const float Fx = a.Fx, Fy = a.Fy, Fz = a.Fz;
     const S *__restrict__ sbase = static_cast<const S *>(a.src);
     S *__restrict__ dbase = static_cast<S *>(a.dst);
     float sdr = 0.f;
-    for (int z = tz; z < nz; z += BZ) {
+    for (int z = wi; z < nz; z += BZ) {
         // Plane offsets i P are recomputed in every iteration from an opaque
         // copy of P: hoisting 19 + 19 plane pointers out of the loop would
         // cost 76 registers.  Element offsets are 32-bit (19 P < 2^32).
@@ -304,79 +316,86 @@ __device__ __forceinline__ float pair_loop(const StepArgs &a, float (*sacc)[9][2
             const int cx = cx_of(i), cz = cz_of(i), cy = cy_of(i);
             const unsigned h = cz > 0 ? hzm : (cz < 0 ? hzp : here);
             const S *row = sbase + (i * Pv + h - cy * nxv);  // (x, y - c_y, z - c_z)
-            const raw cur = PR::ld(row);
+            raw cur;
+            if (active) cur = V::ld(row);
+            else cur = raw{};
             if (cx == 0) v[i] = cur;
-            else if (cx > 0) v[i] = PR::shift_in_left(cur, row - 1, lane);
-            else v[i] = PR::shift_in_right(cur, row + 2, lane);
+            else if (cx > 0) v[i] = V::shift_left(cur, row, side_l);
+            else v[i] = V::shift_right(cur, row, side_r && active);
         }
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
+        for (int j = 0; j < CPL; ++j) {
             float g[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) g[i] = half ? PR::hi(v[i]) : PR::lo(v[i]);
+            for (int i = 0; i < Q; ++i) g[i] = V::cell(v[i], j);
             float rho, ux, uy, uz;
             collide<REG, FORCE>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz);
-            if (half == 0) {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) v[i] = pack_lo(v[i], g[i]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) PR::st(dbase + (i * Pv + here), lo_of(v[i]), g[i]);
-            }
+            for (int i = 0; i < Q; ++i) V::put(v[i], j, g[i]);
             if (STATS) {
-                float *s = &sacc[tz][0][2 * lane + half];
-                s[0 * 2 * BX] += ux; s[1 * 2 * BX] += uy; s[2 * 2 * BX] += uz;
-                s[3 * 2 * BX] += ux * ux; s[4 * 2 * BX] += uy * uy; s[5 * 2 * BX] += uz * uz;
-                s[6 * 2 * BX] += ux * uy; s[7 * 2 * BX] += ux * uz; s[8 * 2 * BX] += uy * uz;
+                float *sp = &sacc[wi][0][CPL * lane + j];
+                constexpr int L = BX * CPL;
+                sp[0 * L] += ux; sp[1 * L] += uy; sp[2 * L] += uz;
+                sp[3 * L] += ux * ux; sp[4 * L] += uy * uy; sp[5 * L] += uz * uz;
+                sp[6 * L] += ux * uy; sp[7 * L] += ux * uz; sp[8 * L] += uy * uz;
             }
-            sdr += rho - 1.0f;
+            if (active) sdr += rho - 1.0f;
+        }
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) V::st(dbase + (i * Pv + here), v[i]);
         }
     }
     return sdr;
 }
 
-// STATS is chosen on the host (it knows the step count): the sampling-step
-// variant is a separate instantiation, so the plain z loop keeps its
-// registers free of the statistics bookkeeping.
+// Interior columns (rows 1..ny-2, x in [32 il, 32 ir)) with CPL cells per
+// lane; the warps of a block are 8 z-lanes of one warp-wide x chunk.  STATS is
+// chosen on the host (it knows the step count): the sampling-step variant is
+// a separate instantiation, so the plain z loop keeps its registers free of
+// the statistics bookkeeping.
 template <typename S, bool REG, bool FORCE, bool STATS>
-__global__ void __launch_bounds__(BX *BZ, 3) lbm_pair_kernel(const StepArgs a)
+__global__ void __launch_bounds__(BX *BZ, sizeof(S) == 4 ? 3 : 2) lbm_vec_kernel(const StepArgs a)
 {
-    __shared__ float sacc[STATS ? BZ : 1][9][2 * BX];  // per-thread statistics slots
+    constexpr int CPL = VecOf<S>::CPL;
+    __shared__ float sacc[STATS ? BZ : 1][9][BX * CPL];  // per-thread statistics slots
     const int nx = a.nx, ny = a.ny;
-    const int c = a.il / 2 + blockIdx.x;   // 64-wide chunk
+    const int lane = threadIdx.x, wi = threadIdx.y;
+    const int k0 = a.il + CPL * blockIdx.x;           // first 32-wide chunk of the block
+    const int k1 = min(k0 + CPL, a.ir);               // one past its last chunk
+    const int x0 = 32 * k0, x_end = 32 * a.ir;
     const int y = blockIdx.y + 1;
-    const int lane = threadIdx.x, tz = threadIdx.y;
     const long long t = a.ctl->t[a.parity];
     const bool do_check = a.check_every > 0 && ((t + 1) % a.check_every) == 0;
     if (STATS) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            sacc[tz][q][2 * lane] = 0.f;
-            sacc[tz][q][2 * lane + 1] = 0.f;
-        }
+        for (int q = 0; q < 9; ++q)
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) sacc[wi][q][CPL * lane + j] = 0.f;
     }
-    const float sdr = pair_loop<S, REG, FORCE, STATS>(a, sacc, c, y);
+    const float sdr = vec_loop<S, REG, FORCE, STATS>(a, sacc, x0, x_end, y);
     if (STATS) {
         __syncthreads();
-        if (tz == 0) {
+        if (wi == 0) {
             const size_t m = (size_t)nx * ny;
 #pragma unroll
-            for (int k2 = 0; k2 < 2; ++k2) {
-                const int col = 2 * lane + k2;
-                const size_t xy = (size_t)y * nx + 64 * c + col;
+            for (int j = 0; j < CPL; ++j) {
+                const int col = CPL * lane + j;
+                if (x0 + col >= x_end) continue;
+                const size_t xy = (size_t)y * nx + x0 + col;
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
-                    double s = 0.0;
-                    for (int k = 0; k < BZ; ++k) s += (double)sacc[k][q][col];
-                    if (q < 3) a.stat_mean[q * m + xy] += s;
-                    else a.stat_rey[(q - 3) * m + xy] += s;
+                    double sum = 0.0;
+                    for (int k = 0; k < BZ; ++k) sum += (double)sacc[k][q][col];
+                    if (q < 3) a.stat_mean[q * m + xy] += sum;
+                    else a.stat_rey[(q - 3) * m + xy] += sum;
                 }
             }
         }
     }
     if (do_check) {
         const int nxc = (nx + BX - 1) / BX;
-        mass_finish<BX * BZ>(a, sdr, y * nxc + 2 * c, y * nxc + 2 * c + 1);
+        mass_finish<BX * BZ>(a, sdr, y * nxc + k0, y * nxc + k0 + 1, y * nxc + k1);
     }
 }
 
@@ -407,41 +426,38 @@ __global__ void __launch_bounds__(BX *BZ, 2) lbm_edge_kernel(const StepArgs a)
 
 int step_grid_blocks(int nx, int ny) { return ((nx + BX - 1) / BX) * ny; }
 
-// Split of the lattice between the interior kernel (pair or scalar) and the
-// edge kernel.  pair: nx even and at least three 64-wide chunks.
+// Split of the lattice between the interior kernel and the edge kernel: the
+// interior is the 32-wide chunks [1, nxc-1) of rows 1..ny-2; the vector
+// kernel (CPL cells per lane) serves it when rows are aligned for its vector
+// width, else the one-cell-per-thread kernel.
 struct Split {
-    bool pair;
+    bool vec;
     int il, ir;           // interior 32-wide chunks [il, ir) of rows 1..ny-2
     int gx, gy;           // interior grid
     int n_edge;
 };
 
-static Split split_of(int nx, int ny, int nz, int interior)
+static Split split_of(int nx, int ny, int nz, int interior, int cpl)
 {
     Split sp{};
     const int nxc = (nx + BX - 1) / BX;
-    const int C = nx / 64;
-    sp.pair = interior != 1 && (nx % 2 == 0) && C >= 3 && ny >= 3 && 19.0 * nx * ny * nz < 4294967296.0;
-    if (sp.pair) {
-        sp.il = 2;
-        sp.ir = 2 * (C - 1);
-        sp.gx = C - 2;
-    } else if (nxc >= 3 && ny >= 3) {
+    if (nxc >= 3 && ny >= 3) {
         sp.il = 1;
         sp.ir = nxc - 1;
-        sp.gx = nxc - 2;
-    } else {
-        sp.il = sp.ir = 0;
-        sp.gx = 0;
-    }
-    sp.gy = (ny >= 3 && sp.gx > 0) ? ny - 2 : 0;
-    if (sp.gy == 0) {
-        sp.il = sp.ir = 0;
-        sp.gx = 0;
+        sp.gy = ny - 2;
+        sp.vec = interior != 1 && nx % cpl == 0 && 19.0 * nx * ny * nz < 4294967296.0;
+        sp.gx = sp.vec ? (sp.ir - sp.il + cpl - 1) / cpl : sp.ir - sp.il;
     }
     const int nwall = (ny >= 2 ? 2 : 1) * nxc;
     sp.n_edge = nwall + (ny > 2 ? ny - 2 : 0) * (nxc - (sp.ir - sp.il));
     return sp;
+}
+
+// the TMA-staged kernel is used on request only (STG_LBM_INTERIOR=tma) and
+// needs 16-byte rows and an even number of interior 32-wide chunks
+static bool use_tma(const StepArgs &a, const Split &sp, const void *tmap)
+{
+    return sp.vec && tmap && a.interior == 3 && (sp.ir - sp.il) % 2 == 0;
 }
 
 template <typename S, bool REG, bool FORCE>
@@ -453,11 +469,11 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
     if (sp.gx > 0 && sp.gy > 0) {
         const dim3 grid(sp.gx, sp.gy);
         const int storage = sizeof(S) == 4 ? 0 : 1;
-        if (sp.pair && tmap && a.interior != 2 && tma_usable(a.nx, storage)) {
-            launch_tma(a, tmap, sp.gx, sp.gy, storage, REG ? 0 : 1, stats, s);
-        } else if (sp.pair) {
-            if (stats) lbm_pair_kernel<S, REG, FORCE, true><<<grid, block, 0, s>>>(a);
-            else lbm_pair_kernel<S, REG, FORCE, false><<<grid, block, 0, s>>>(a);
+        if (use_tma(a, sp, tmap) && tma_usable(a.nx, storage)) {
+            launch_tma(a, tmap, (sp.ir - sp.il) / 2, sp.gy, storage, REG ? 0 : 1, stats, s);
+        } else if (sp.vec) {
+            if (stats) lbm_vec_kernel<S, REG, FORCE, true><<<grid, block, 0, s>>>(a);
+            else lbm_vec_kernel<S, REG, FORCE, false><<<grid, block, 0, s>>>(a);
         } else {
             lbm_step_kernel<S, REG, FORCE><<<grid, block, 0, s>>>(a);
         }
@@ -467,11 +483,12 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
 template <typename S, bool REG>
 static void launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaStream_t s, cudaStream_t side)
 {
-    const Split sp = split_of(a0.nx, a0.ny, a0.nz, a0.interior);
+    const Split sp = split_of(a0.nx, a0.ny, a0.nz, a0.interior, VecOf<S>::CPL);
     StepArgs a = a0;
     a.il = sp.il;
     a.ir = sp.ir;
-    a.total_blocks = (unsigned)(sp.n_edge + sp.gx * sp.gy);
+    const bool tma = use_tma(a, sp, tmap) && tma_usable(a.nx, sizeof(S) == 4 ? 0 : 1);
+    a.total_blocks = (unsigned)(sp.n_edge + (tma ? (sp.ir - sp.il) / 2 : sp.gx) * sp.gy);
     if (a.has_force) launch_forced<S, REG, true>(a, sp, stats, tmap, s, side);
     else launch_forced<S, REG, false>(a, sp, stats, tmap, s, side);
 }

@@ -1,6 +1,6 @@
 // Interior columns of the fused step with the pull staged by the TMA engine.
 //
-// A block is TW warps on one 64-wide x chunk at one y.  The z-planes are taken
+// A block is TW warps on one 64-wide x chunk (from x = 32 il) at one y.  The z-planes are taken
 // in groups of TW (warp w owns plane z = TW g + w of group g).  For each group
 // and each population i one tiled tensor copy (a box of 80 x-values, 1 row,
 // TW planes of plane i, starting at (x0 - 8, y - c_iy, TW g - c_iz)) lands in
@@ -168,9 +168,8 @@ __global__ void __launch_bounds__(32 * TW, 6) lbm_tma_kernel(const StepArgs a, c
 
     const int w = threadIdx.y, lane = threadIdx.x;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int c = a.il / 2 + blockIdx.x;
     const int y = blockIdx.y + 1;
-    const int x0 = 64 * c;
+    const int x0 = 32 * a.il + 64 * blockIdx.x;  // interior chunk pairs from x = 32 il
     const int ngroups = (nz + TW - 1) / TW;
     const long long t = a.ctl->t[a.parity];
     const bool do_check = a.check_every > 0 && ((t + 1) % a.check_every) == 0;
@@ -302,7 +301,8 @@ __global__ void __launch_bounds__(32 * TW, 6) lbm_tma_kernel(const StepArgs a, c
     }
     if (do_check) {
         const int nxc = (nx + 31) / 32;
-        mass_finish<32 * TW>(a, sdr, y * nxc + 2 * c, y * nxc + 2 * c + 1);
+        const int k0 = a.il + 2 * blockIdx.x;
+        mass_finish<32 * TW>(a, sdr, y * nxc + k0, y * nxc + k0 + 1, y * nxc + k0 + 2);
     }
 }
 
