@@ -32,6 +32,8 @@ struct StepArgs {
     int il, ir;             // 32-wide x chunks [il, ir) of rows 1..ny-2 belong to the interior kernel
     int interior;           // interior kernel: 0 best available, 1 one cell per thread, 2 cell pairs, 3 TMA-staged
     unsigned total_blocks;  // blocks of all step kernels of the pass (mass-check completion count)
+    int slot_base;          // first mass-partial slot of this launch's blocks
+    int bump_t;             // this launch advances the device step counter
     int nx, ny, nz;
     unsigned P;           // cells per population plane (nx*ny*nz)
     int bc_x, bc_y;       // STG_BC_X_*, STG_BC_Y_*

@@ -6,12 +6,12 @@
 namespace stg {
 
 // Deterministic FP64 mass of a step pass: each block leaves the sum of its
-// threads' (rho - 1) at mass_partial[part] and 0 in the slots [zb, ze) of the
-// other 32-wide columns it covers; the last of all total_blocks blocks adds
-// the ceil(nx/32) * ny partials in index order and writes nx ny nz + sum.
-// NT = threads per block (a power of two, at most 256).
+// threads' (rho - 1) in its own slot, a.slot_base + its linear block index;
+// the last of all total_blocks blocks of the pass (all kernels) adds the
+// slots in index order and writes nx ny nz + sum.  NT = threads per block (a
+// power of two, at most 256).
 template <int NT>
-__device__ __forceinline__ void mass_finish(const StepArgs &a, float sdr, int part, int zb, int ze)
+__device__ __forceinline__ void mass_finish(const StepArgs &a, float sdr)
 {
     __shared__ double rd[NT];
     __shared__ int s_last;
@@ -22,10 +22,8 @@ __device__ __forceinline__ void mass_finish(const StepArgs &a, float sdr, int pa
         if (tid < off) rd[tid] += rd[tid + off];
         __syncthreads();
     }
-    const unsigned nparts = (unsigned)((a.nx + 31) / 32) * a.ny;
     if (tid == 0) {
-        a.mass_partial[part] = rd[0];
-        for (int k = zb; k < ze; ++k) a.mass_partial[k] = 0.0;
+        a.mass_partial[a.slot_base + blockIdx.y * gridDim.x + blockIdx.x] = rd[0];
         __threadfence();
         const unsigned prev = atomicAdd(a.mass_counter, 1u);
         s_last = (prev == a.total_blocks - 1);
@@ -34,7 +32,7 @@ __device__ __forceinline__ void mass_finish(const StepArgs &a, float sdr, int pa
     if (s_last) {
         __threadfence();
         double acc = 0.0;
-        for (unsigned k = tid; k < nparts; k += NT) acc += __ldcg(a.mass_partial + k);
+        for (unsigned k = tid; k < a.total_blocks; k += NT) acc += __ldcg(a.mass_partial + k);
         rd[tid] = acc;
         __syncthreads();
         for (int off = NT / 2; off > 0; off >>= 1) {

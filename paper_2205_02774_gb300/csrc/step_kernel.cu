@@ -190,7 +190,7 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
             }
         }
     }
-    if (do_check) mass_finish<BX * BZ>(a, sdr, y * ((nx + BX - 1) / BX) + bx, 0, 0);
+    if (do_check) mass_finish<BX * BZ>(a, sdr);
 }
 
 // Scalar interior columns: x chunks [il, ir), y = 1..ny-2 (odd nx or narrow lattices).
@@ -202,13 +202,13 @@ __global__ void __launch_bounds__(BX *BZ, 4) lbm_step_kernel(const StepArgs a)
 
 // ---------------------------------------------------------------------------
 // Several cells per lane: lane l of a warp owns CPL consecutive cells starting
-// at x = x0 + CPL l, so every population row is read and written as aligned
-// vectors (FP32: 2 cells, 8 B; FP16: 4 cells, 8 B), 256 B per warp
-// instruction.  A pull with c_x = +1 needs the cells shifted by one: the
+// at x = 32 CPL b + CPL l, so every population row is read and written as
+// aligned vectors (FP32 pairs: 8 B, 256 B per warp instruction; FP16 pairs:
+// 4 B, 128 B).  A pull with c_x = +1 needs the cells shifted by one: the
 // missing x-1 value is the top cell of the left lane's vector (warp shuffle;
-// lane 0 reads it directly), and c_x = -1 mirrors this on the right (the last
-// active lane reads it directly).  The wide accesses keep enough bytes in
-// flight per SM to saturate HBM, which 2-byte accesses cannot.
+// lane 0 reads it directly, wrapping in x when x is periodic), and c_x = -1
+// mirrors this on the right.  The wide accesses keep enough bytes in flight
+// per SM to saturate HBM, which 2-byte accesses cannot.
 template <typename S, int CPL>
 struct Vec;
 
@@ -223,23 +223,27 @@ struct Vec<float, 2> {
         else v.x = f;
     }
     static __device__ __forceinline__ void st(float *p, raw v) { __stcs(reinterpret_cast<float2 *>(p), v); }
-    // (x-1, x) from the left lane's (x-2, x-1) and ours (x, x+1)
-    static __device__ __forceinline__ raw shift_left(raw cur, const float *p, bool side)
+    static __device__ __forceinline__ void st1(float *p, raw v, int j) { __stcs(p + j, cell(v, j)); }
+    // (x-1, x) from the left lane's (x-2, x-1) and ours (x, x+1); xl = x-1 when read directly
+    static __device__ __forceinline__ raw shift_left(raw cur, const float *xl, bool side)
     {
         float l = __shfl_up_sync(0xffffffffu, cur.y, 1);
-        if (side) l = __ldg(p - 1);
+        if (side) l = __ldg(xl);
         return make_float2(l, cur.x);
     }
-    // (x+1, x+2) from ours and the right lane's (x+2, x+3)
-    static __device__ __forceinline__ raw shift_right(raw cur, const float *p, bool side)
+    // (x+1, x+2) from ours and the right lane's (x+2, x+3); xr = x+2 when read directly
+    static __device__ __forceinline__ raw shift_right(raw cur, const float *xr, bool side)
     {
         float r = __shfl_down_sync(0xffffffffu, cur.x, 1);
-        if (side) r = __ldg(p + 2);
+        if (side) r = __ldg(xr);
         return make_float2(cur.y, r);
     }
 };
 
-__device__ __forceinline__ float h2f(unsigned v, int hi) { return __half2float(__ushort_as_half((unsigned short)(hi ? v >> 16 : v & 0xffffu))); }
+__device__ __forceinline__ float h2f(unsigned v, int hi)
+{
+    return __half2float(__ushort_as_half((unsigned short)(hi ? v >> 16 : v & 0xffffu)));
+}
 __device__ __forceinline__ unsigned f2h(float f) { return (unsigned)__half_as_ushort(__float2half_rn(f)); }
 
 template <>
@@ -253,37 +257,74 @@ struct Vec<__half, 4> {
         w = (j & 1) ? ((w & 0xffffu) | (f2h(f) << 16)) : ((w & 0xffff0000u) | f2h(f));
     }
     static __device__ __forceinline__ void st(__half *p, raw v) { __stcs(reinterpret_cast<uint2 *>(p), v); }
+    static __device__ __forceinline__ void st1(__half *p, raw v, int j)
+    {
+        const unsigned w = j < 2 ? v.x : v.y;
+        __stcs(p + j, __ushort_as_half((unsigned short)((j & 1) ? w >> 16 : w & 0xffffu)));
+    }
     // (x-1, x, x+1, x+2)
-    static __device__ __forceinline__ raw shift_left(raw cur, const __half *p, bool side)
+    static __device__ __forceinline__ raw shift_left(raw cur, const __half *xl, bool side)
     {
         unsigned l = __shfl_up_sync(0xffffffffu, cur.y, 1);
-        if (side) l = (unsigned)__half_as_ushort(__ldg(p - 1)) << 16;
+        if (side) l = (unsigned)__half_as_ushort(__ldg(xl)) << 16;
         return make_uint2(__byte_perm(l, cur.x, 0x5432), __byte_perm(cur.x, cur.y, 0x5432));
     }
-    // (x+1, x+2, x+3, x+4)
-    static __device__ __forceinline__ raw shift_right(raw cur, const __half *p, bool side)
+    // (x+1, x+2, x+3, x+4); xr = x+4 when read directly
+    static __device__ __forceinline__ raw shift_right(raw cur, const __half *xr, bool side)
     {
         unsigned r = __shfl_down_sync(0xffffffffu, cur.x, 1);
-        if (side) r = (unsigned)__half_as_ushort(__ldg(p + 4));
+        if (side) r = (unsigned)__half_as_ushort(__ldg(xr));
         return make_uint2(__byte_perm(cur.x, cur.y, 0x5432), __byte_perm(cur.y, r, 0x5432));
     }
 };
 
+template <>
+struct Vec<__half, 2> {
+    using raw = unsigned;  // two binary16: low half = first cell
+    static __device__ __forceinline__ raw ld(const __half *p) { return __ldg(reinterpret_cast<const unsigned *>(p)); }
+    static __device__ __forceinline__ float cell(raw v, int j) { return h2f(v, j); }
+    static __device__ __forceinline__ void put(raw &v, int j, float f)
+    {
+        v = j ? ((v & 0xffffu) | (f2h(f) << 16)) : ((v & 0xffff0000u) | f2h(f));
+    }
+    static __device__ __forceinline__ void st(__half *p, raw v) { __stcs(reinterpret_cast<unsigned *>(p), v); }
+    static __device__ __forceinline__ void st1(__half *p, raw v, int j)
+    {
+        __stcs(p + j, __ushort_as_half((unsigned short)(j ? v >> 16 : v & 0xffffu)));
+    }
+    // (x-1, x)
+    static __device__ __forceinline__ raw shift_left(raw cur, const __half *xl, bool side)
+    {
+        unsigned l = __shfl_up_sync(0xffffffffu, cur, 1);
+        if (side) l = (unsigned)__half_as_ushort(__ldg(xl)) << 16;
+        return __byte_perm(l, cur, 0x5432);
+    }
+    // (x+1, x+2); xr = x+2 when read directly
+    static __device__ __forceinline__ raw shift_right(raw cur, const __half *xr, bool side)
+    {
+        unsigned r = __shfl_down_sync(0xffffffffu, cur, 1);
+        if (side) r = (unsigned)__half_as_ushort(__ldg(xr));
+        return __byte_perm(cur, r, 0x5432);
+    }
+};
+
+// cells per lane: 2 for both storages (FP32 8-byte pairs, FP16 4-byte pairs);
+// Vec<__half, 4> (8-byte quads) is kept for lattices where its 128-register
+// footprint pays off.
 template <typename S>
 struct VecOf {
     static constexpr int CPL = 2;
 };
-template <>
-struct VecOf<__half> {
-    static constexpr int CPL = 4;
-};
 
-// z loop of one vector column: x0 is the warp's first cell, x_end one past
-// the interior's last cell.  STATS adds the per-cell velocity sums to the
-// block's shared-memory slots.  Returns the thread's sum of rho - 1.
-template <typename S, bool REG, bool FORCE, bool STATS>
-__device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX * VecOf<S>::CPL], int x0, int x_end,
-                                          int y)
+// One vector column (CPL 32 cells wide) at row y over all z.  YEDGE rows
+// (y = 0 or ny-1) take the y neighbour by half-way bounce-back (walls: the
+// cell's own opposite population) or by the periodic wrap.  In inlet/outlet
+// mode the cells x = 0 and x = nx-1 are left to the boundary kernel: their
+// (meaningless) values are neither stored nor counted.  STATS adds the
+// per-cell velocity sums to the block's shared-memory slots.  Returns the
+// thread's sum of rho - 1.
+template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE>
+__device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX * VecOf<S>::CPL], int x0, int y)
 {
     constexpr int CPL = VecOf<S>::CPL;
     using V = Vec<S, CPL>;
@@ -292,9 +333,30 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
     const int nxy = nx * ny;
     const int lane = threadIdx.x, wi = threadIdx.y;
     const int x = x0 + CPL * lane;
-    const bool active = x < x_end;
+    const bool active = x < nx;
+    const bool inout = a.bc_x == 0;
+    // x halo read directly by lane 0 / by the last active lane
     const bool side_l = lane == 0;
-    const bool side_r = lane == 31 || x + CPL == x_end;
+    const bool side_r = active && (lane == 31 || x + CPL == nx);
+    const int xl = x == 0 ? (inout ? 0 : nx - 1) : x - 1;        // element read for x-1
+    const int xr = x + CPL == nx ? (inout ? nx - 1 : 0) : x + CPL; // element read for x+CPL
+    // cells excluded in inlet/outlet mode (handled by the boundary kernel)
+    const bool skip_lo = inout && x == 0;
+    const bool skip_hi = inout && x + CPL == nx;
+    // y neighbours of this row (YEDGE rows only)
+    bool ym_bb = false, yp_bb = false;
+    int ym_off = nx, yp_off = -nx;  // element offset of the source row for c_y = +1 / -1 (subtracted)
+    if (YEDGE) {
+        const bool walls = a.bc_y == 0;
+        if (y == 0) {
+            if (walls) ym_bb = true;
+            else ym_off = -(ny - 1) * nx;
+        }
+        if (y == ny - 1) {
+            if (walls) yp_bb = true;
+            else yp_off = (ny - 1) * nx;
+        }
+    }
     const float tau0 = a.tau0, kq = a.kq;
     const float Fx = a.Fx, Fy = a.Fy, Fz = a.Fz;
     const S *__restrict__ sbase = static_cast<const S *>(a.src);
@@ -307,21 +369,33 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
         unsigned Pv, nxv;
         asm volatile("mov.u32 %0, %1;" : "=r"(Pv) : "r"(a.P));
         asm volatile("mov.u32 %0, %1;" : "=r"(nxv) : "r"((unsigned)nx));
-        const unsigned here = ((unsigned)z * ny + y) * nx + x;
-        const unsigned hzm = here - ((z == 0) ? -(nz - 1) * nxy : nxy);
-        const unsigned hzp = here - ((z == nz - 1) ? (nz - 1) * nxy : -nxy);
+        const unsigned row0 = ((unsigned)z * ny + y) * nx;
+        const unsigned here = row0 + x;
+        const unsigned dzm = (z == 0) ? -(nz - 1) * nxy : nxy;
+        const unsigned dzp = (z == nz - 1) ? (nz - 1) * nxy : -nxy;
         raw v[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int cx = cx_of(i), cz = cz_of(i), cy = cy_of(i);
-            const unsigned h = cz > 0 ? hzm : (cz < 0 ? hzp : here);
-            const S *row = sbase + (i * Pv + h - cy * nxv);  // (x, y - c_y, z - c_z)
+            const bool bb = YEDGE && ((cy > 0 && ym_bb) || (cy < 0 && yp_bb));
+            if (bb) {
+                // half-way bounce-back: f_i(x) = f*_opp(i)(x), same cell
+                raw cur;
+                if (active) cur = V::ld(sbase + (opp_of(i) * Pv + here));
+                else cur = raw{};
+                v[i] = cur;
+                continue;
+            }
+            const unsigned dz = cz > 0 ? dzm : (cz < 0 ? dzp : 0u);
+            const unsigned dy = cy > 0 ? (YEDGE ? (unsigned)ym_off : nxv) : (cy < 0 ? (YEDGE ? (unsigned)yp_off : 0u - nxv) : 0u);
+            const unsigned rbase = i * Pv + row0 - dz - dy;  // plane i, row (y - c_y, z - c_z)
+            const S *row = sbase + (rbase + x);
             raw cur;
             if (active) cur = V::ld(row);
             else cur = raw{};
             if (cx == 0) v[i] = cur;
-            else if (cx > 0) v[i] = V::shift_left(cur, row, side_l);
-            else v[i] = V::shift_right(cur, row, side_r && active);
+            else if (cx > 0) v[i] = V::shift_left(cur, sbase + (rbase + xl), side_l && !(inout && x == 0));
+            else v[i] = V::shift_right(cur, sbase + (rbase + xr), side_r && !(inout && x + CPL == nx));
         }
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
@@ -332,39 +406,47 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
             collide<REG, FORCE>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz);
 #pragma unroll
             for (int i = 0; i < Q; ++i) V::put(v[i], j, g[i]);
-            if (STATS) {
+            const bool counted = active && !(j == 0 && skip_lo) && !(j == CPL - 1 && skip_hi);
+            if (STATS && counted) {
                 float *sp = &sacc[wi][0][CPL * lane + j];
                 constexpr int L = BX * CPL;
                 sp[0 * L] += ux; sp[1 * L] += uy; sp[2 * L] += uz;
                 sp[3 * L] += ux * ux; sp[4 * L] += uy * uy; sp[5 * L] += uz * uz;
                 sp[6 * L] += ux * uy; sp[7 * L] += ux * uz; sp[8 * L] += uy * uz;
             }
-            if (active) sdr += rho - 1.0f;
+            if (counted) sdr += rho - 1.0f;
         }
         if (active) {
+            if (!skip_lo && !skip_hi) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) V::st(dbase + (i * Pv + here), v[i]);
+                for (int i = 0; i < Q; ++i) V::st(dbase + (i * Pv + here), v[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < Q; ++i)
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j)
+                        if (!(j == 0 && skip_lo) && !(j == CPL - 1 && skip_hi)) V::st1(dbase + (i * Pv + here), v[i], j);
+            }
         }
     }
     return sdr;
 }
 
-// Interior columns (rows 1..ny-2, x in [32 il, 32 ir)) with CPL cells per
-// lane; the warps of a block are 8 z-lanes of one warp-wide x chunk.  STATS is
-// chosen on the host (it knows the step count): the sampling-step variant is
-// a separate instantiation, so the plain z loop keeps its registers free of
-// the statistics bookkeeping.
-template <typename S, bool REG, bool FORCE, bool STATS>
-__global__ void __launch_bounds__(BX *BZ, sizeof(S) == 4 ? 3 : 2) lbm_vec_kernel(const StepArgs a)
+// Vector kernel over all x of rows 1..ny-2 (YEDGE false) or of rows 0 and
+// ny-1 (YEDGE true; that launch also advances the device step counter).  The
+// warps of a block are 8 z-lanes of one CPL*32-wide x chunk.  STATS is chosen
+// on the host (it knows the step count): the sampling-step variant is a
+// separate instantiation, so the plain z loop keeps its registers free of the
+// statistics bookkeeping.
+template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE>
+__global__ void __launch_bounds__(BX *BZ, VecOf<S>::CPL == 2 ? 3 : 2) lbm_vec_kernel(const StepArgs a)
 {
     constexpr int CPL = VecOf<S>::CPL;
     __shared__ float sacc[STATS ? BZ : 1][9][BX * CPL];  // per-thread statistics slots
     const int nx = a.nx, ny = a.ny;
     const int lane = threadIdx.x, wi = threadIdx.y;
-    const int k0 = a.il + CPL * blockIdx.x;           // first 32-wide chunk of the block
-    const int k1 = min(k0 + CPL, a.ir);               // one past its last chunk
-    const int x0 = 32 * k0, x_end = 32 * a.ir;
-    const int y = blockIdx.y + 1;
+    const int x0 = BX * CPL * blockIdx.x;
+    const int y = YEDGE ? (blockIdx.y == 0 ? 0 : ny - 1) : blockIdx.y + 1;
     const long long t = a.ctl->t[a.parity];
     const bool do_check = a.check_every > 0 && ((t + 1) % a.check_every) == 0;
     if (STATS) {
@@ -373,35 +455,128 @@ __global__ void __launch_bounds__(BX *BZ, sizeof(S) == 4 ? 3 : 2) lbm_vec_kernel
 #pragma unroll
             for (int j = 0; j < CPL; ++j) sacc[wi][q][CPL * lane + j] = 0.f;
     }
-    const float sdr = vec_loop<S, REG, FORCE, STATS>(a, sacc, x0, x_end, y);
+    const float sdr = vec_loop<S, REG, FORCE, STATS, YEDGE>(a, sacc, x0, y);
     if (STATS) {
         __syncthreads();
         if (wi == 0) {
             const size_t m = (size_t)nx * ny;
+            const bool inout = a.bc_x == 0;
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
-                const int col = CPL * lane + j;
-                if (x0 + col >= x_end) continue;
-                const size_t xy = (size_t)y * nx + x0 + col;
+                const int xc = x0 + CPL * lane + j;
+                if (xc >= nx || (inout && (xc == 0 || xc == nx - 1))) continue;
+                const size_t xy = (size_t)y * nx + xc;
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
                     double sum = 0.0;
-                    for (int k = 0; k < BZ; ++k) sum += (double)sacc[k][q][col];
+                    for (int k = 0; k < BZ; ++k) sum += (double)sacc[k][q][CPL * lane + j];
                     if (q < 3) a.stat_mean[q * m + xy] += sum;
                     else a.stat_rey[(q - 3) * m + xy] += sum;
                 }
             }
         }
     }
-    if (do_check) {
-        const int nxc = (nx + BX - 1) / BX;
-        mass_finish<BX * BZ>(a, sdr, y * nxc + k0, y * nxc + k0 + 1, y * nxc + k1);
-    }
+    if (do_check) mass_finish<BX * BZ>(a, sdr);
+    if (YEDGE && a.bump_t && blockIdx.x == 0 && blockIdx.y == 0 && lane == 0 && wi == 0)
+        a.ctl->t[a.parity ^ 1] = t + 1;
 }
 
-// Edge columns (32 wide, one cell per thread, general pull): every chunk of
-// rows 0 and ny-1, and the chunks outside [il, ir) of rows 1..ny-2.  Block 0
-// also advances the device step counter (read by the next step only).
+// Inlet (x = 0) and outlet (x = nx-1) cells: block (side, y), threads over z,
+// one cell per thread through the general pull and the regularized rebuild.
+constexpr int XB_THREADS = 128;
+
+template <typename S, bool REG, bool FORCE>
+__global__ void __launch_bounds__(XB_THREADS) lbm_xbound_kernel(const StepArgs a)
+{
+    __shared__ float red[9][XB_THREADS];
+    const S *__restrict__ src = static_cast<const S *>(a.src);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const unsigned P = a.P;
+    const int x = blockIdx.x == 0 ? 0 : nx - 1;
+    const int y = blockIdx.y;
+    const int tid = threadIdx.x;
+    const long long t = a.ctl->t[a.parity];
+    const bool do_stats = a.stats_every > 0 && ((t + 1) % a.stats_every) == 0;
+    const bool do_check = a.check_every > 0 && ((t + 1) % a.check_every) == 0;
+    const float tau0 = a.tau0, kq = a.kq;
+    const float Fx = a.Fx, Fy = a.Fy, Fz = a.Fz;
+    const int xm = max(x - 1, 0), xp = min(x + 1, nx - 1);
+    const bool xm_ok = x - 1 >= 0, xp_ok = x + 1 < nx;
+    int ym = y - 1, yp = y + 1;
+    bool ym_w = false, yp_w = false;
+    if (a.bc_y == 0) {
+        ym_w = ym < 0;
+        yp_w = yp >= ny;
+        ym = max(ym, 0);
+        yp = min(yp, ny - 1);
+    } else {
+        if (ym < 0) ym += ny;
+        if (yp >= ny) yp -= ny;
+    }
+    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float sdr = 0.f;
+    for (int z = tid; z < nz; z += XB_THREADS) {
+        const int zm = (z == 0) ? nz - 1 : z - 1;
+        const int zp = (z == nz - 1) ? 0 : z + 1;
+        const unsigned here = ((unsigned)z * ny + y) * nx + x;
+        float g[Q];
+        gather_general<S>(src, P, nx, ny, x, y, z, xm, xp, xm_ok, xp_ok, ym, yp, ym_w, yp_w, zm, zp, here, g);
+        if (x == 0) {
+            const size_t pc = (size_t)z * ny + y, pl3 = (size_t)ny * nz;
+            const float ubx = a.ubc[pc], uby = a.ubc[pl3 + pc], ubz = a.ubc[2 * pl3 + pc];
+            // Zou-He density, eq. (density_bc): parallel set + 2 x leaving set.
+            // The weights of that combination sum to 1 (2/3 + 2 x 1/6), so
+            // rho_bc - 1 = (S_g + u_x)/(1 - u_x) with S_g the same sum of g.
+            float par = 0.f, lv = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (cx_of(i) == 0) par += g[i];
+                if (cx_of(i) < 0) lv += g[i];
+            }
+            rebuild<1>(g, (par + 2.0f * lv + ubx) / (1.0f - ubx), ubx, uby, ubz);
+        } else {
+            // zero-gradient velocity from the stored column x = nx-2, rho = 1
+            const unsigned nb = ((unsigned)z * ny + y) * nx + (nx - 2);
+            float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float v = Pop<S>::ld(src + (size_t)i * P + nb);
+                r += v;
+                jx += cx_of(i) * v;
+                jy += cy_of(i) * v;
+                jz += cz_of(i) * v;
+            }
+            const float ir = 1.0f / (1.0f + r);
+            rebuild<-1>(g, 0.0f, jx * ir, jy * ir, jz * ir);
+        }
+        float rho, ux, uy, uz;
+        collide<REG, FORCE>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Pop<S>::st(static_cast<S *>(a.dstp[i]) + here, g[i]);
+        acc[0] += ux; acc[1] += uy; acc[2] += uz;
+        acc[3] += ux * ux; acc[4] += uy * uy; acc[5] += uz * uz;
+        acc[6] += ux * uy; acc[7] += ux * uz; acc[8] += uy * uz;
+        sdr += rho - 1.0f;
+    }
+    if (do_stats) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) red[q][tid] = acc[q];
+        __syncthreads();
+        if (tid < 9) {
+            double sum = 0.0;
+            for (int k = 0; k < XB_THREADS; ++k) sum += (double)red[tid][k];
+            const size_t m = (size_t)nx * ny, xy = (size_t)y * nx + x;
+            if (tid < 3) a.stat_mean[tid * m + xy] += sum;
+            else a.stat_rey[(tid - 3) * m + xy] += sum;
+        }
+    }
+    if (do_check) mass_finish<XB_THREADS>(a, sdr);
+}
+
+// Edge columns of the one-cell-per-thread split (32 wide, general pull):
+// every chunk of rows 0 and ny-1, and the chunks outside [il, ir) of rows
+// 1..ny-2.  Block 0 also advances the device step counter (read by the next
+// step only).
 template <typename S, bool REG, bool FORCE>
 __global__ void __launch_bounds__(BX *BZ, 2) lbm_edge_kernel(const StepArgs a)
 {
@@ -421,43 +596,45 @@ __global__ void __launch_bounds__(BX *BZ, 2) lbm_edge_kernel(const StepArgs a)
     }
     const long long t = a.ctl->t[a.parity];
     step_column<S, REG, FORCE, true>(a, bx, y);
-    if (b == 0 && threadIdx.x == 0 && threadIdx.y == 0) a.ctl->t[a.parity ^ 1] = t + 1;
+    if (a.bump_t && b == 0 && threadIdx.x == 0 && threadIdx.y == 0) a.ctl->t[a.parity ^ 1] = t + 1;
 }
 
-int step_grid_blocks(int nx, int ny) { return ((nx + BX - 1) / BX) * ny; }
+// Upper bound of the mass-partial slots a step pass uses (one per block).
+int step_grid_blocks(int nx, int ny) { return ((nx + BX - 1) / BX) * ny + 2 * ny + 64; }
 
-// Split of the lattice between the interior kernel and the edge kernel: the
-// interior is the 32-wide chunks [1, nxc-1) of rows 1..ny-2; the vector
-// kernel (CPL cells per lane) serves it when rows are aligned for its vector
-// width, else the one-cell-per-thread kernel.
+// How a pass covers the lattice.
+//  vector split: vector kernel on rows 1..ny-2 and on rows {0, ny-1} (all x),
+//                boundary kernel on x = 0 and x = nx-1 (inlet/outlet only);
+//  scalar split: interior kernel (one cell per thread, or TMA-staged) on the
+//                32-wide chunks [1, nxc-1) of rows 1..ny-2, edge kernel on the
+//                rest.
 struct Split {
     bool vec;
-    int il, ir;           // interior 32-wide chunks [il, ir) of rows 1..ny-2
-    int gx, gy;           // interior grid
+    int nxv;                   // vector chunks per row
+    int il, ir, gx, gy;        // scalar split interior
     int n_edge;
 };
 
-static Split split_of(int nx, int ny, int nz, int interior, int cpl)
+static Split split_of(const StepArgs &a, int cpl)
 {
     Split sp{};
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int nxc = (nx + BX - 1) / BX;
+    sp.vec = (a.interior == 0 || a.interior == 2) && nx % cpl == 0 && nx >= 2 * cpl &&
+             19.0 * nx * ny * nz < 4294967296.0 && (a.bc_x != 0 || nx >= 3);
+    if (sp.vec) {
+        sp.nxv = (nx + BX * cpl - 1) / (BX * cpl);
+        return sp;
+    }
     if (nxc >= 3 && ny >= 3) {
         sp.il = 1;
         sp.ir = nxc - 1;
         sp.gy = ny - 2;
-        sp.vec = interior != 1 && nx % cpl == 0 && 19.0 * nx * ny * nz < 4294967296.0;
-        sp.gx = sp.vec ? (sp.ir - sp.il + cpl - 1) / cpl : sp.ir - sp.il;
+        sp.gx = sp.ir - sp.il;
     }
     const int nwall = (ny >= 2 ? 2 : 1) * nxc;
     sp.n_edge = nwall + (ny > 2 ? ny - 2 : 0) * (nxc - (sp.ir - sp.il));
     return sp;
-}
-
-// the TMA-staged kernel is used on request only (STG_LBM_INTERIOR=tma) and
-// needs 16-byte rows and an even number of interior 32-wide chunks
-static bool use_tma(const StepArgs &a, const Split &sp, const void *tmap)
-{
-    return sp.vec && tmap && a.interior == 3 && (sp.ir - sp.il) % 2 == 0;
 }
 
 template <typename S, bool REG, bool FORCE>
@@ -465,37 +642,59 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
                           cudaStream_t side)
 {
     const dim3 block(BX, BZ);
-    lbm_edge_kernel<S, REG, FORCE><<<sp.n_edge, block, 0, side>>>(a);
-    if (sp.gx > 0 && sp.gy > 0) {
-        const dim3 grid(sp.gx, sp.gy);
-        const int storage = sizeof(S) == 4 ? 0 : 1;
-        if (use_tma(a, sp, tmap) && tma_usable(a.nx, storage)) {
-            launch_tma(a, tmap, (sp.ir - sp.il) / 2, sp.gy, storage, REG ? 0 : 1, stats, s);
-        } else if (sp.vec) {
-            if (stats) lbm_vec_kernel<S, REG, FORCE, true><<<grid, block, 0, s>>>(a);
-            else lbm_vec_kernel<S, REG, FORCE, false><<<grid, block, 0, s>>>(a);
-        } else {
-            lbm_step_kernel<S, REG, FORCE><<<grid, block, 0, s>>>(a);
+    const int storage = sizeof(S) == 4 ? 0 : 1;
+    if (sp.vec) {
+        const int ny = a.ny;
+        const int rows_in = ny > 2 ? ny - 2 : 0, rows_edge = ny >= 2 ? 2 : 1;
+        const int n_in = sp.nxv * rows_in, n_edge = sp.nxv * rows_edge;
+        const int n_xb = a.bc_x == 0 ? 2 * ny : 0;
+        a.total_blocks = (unsigned)(n_in + n_edge + n_xb);
+        StepArgs ai = a, ae = a, ab = a;
+        ai.slot_base = 0;
+        ae.slot_base = n_in;
+        ab.slot_base = n_in + n_edge;
+        ae.bump_t = 1;
+        if (n_in > 0) {
+            const dim3 g(sp.nxv, rows_in);
+            if (stats) lbm_vec_kernel<S, REG, FORCE, true, false><<<g, block, 0, s>>>(ai);
+            else lbm_vec_kernel<S, REG, FORCE, false, false><<<g, block, 0, s>>>(ai);
         }
+        const dim3 ge(sp.nxv, rows_edge);
+        if (stats) lbm_vec_kernel<S, REG, FORCE, true, true><<<ge, block, 0, side>>>(ae);
+        else lbm_vec_kernel<S, REG, FORCE, false, true><<<ge, block, 0, side>>>(ae);
+        if (n_xb > 0) lbm_xbound_kernel<S, REG, FORCE><<<dim3(2, ny), XB_THREADS, 0, side>>>(ab);
+        return;
+    }
+    const bool tma = a.interior == 3 && tmap && sp.gx > 0 && sp.gy > 0 && (sp.ir - sp.il) % 2 == 0 &&
+                     a.nx % 2 == 0 && 19.0 * a.nx * a.ny * a.nz < 4294967296.0 && tma_usable(a.nx, storage);
+    const int n_in = sp.gy > 0 ? (tma ? (sp.ir - sp.il) / 2 : sp.gx) * sp.gy : 0;
+    a.il = sp.il;
+    a.ir = sp.ir;
+    a.total_blocks = (unsigned)(n_in + sp.n_edge);
+    StepArgs ai = a, ae = a;
+    ai.slot_base = 0;
+    ae.slot_base = n_in;
+    ae.bump_t = 1;
+    lbm_edge_kernel<S, REG, FORCE><<<sp.n_edge, block, 0, side>>>(ae);
+    if (n_in > 0) {
+        if (tma) launch_tma(ai, tmap, (sp.ir - sp.il) / 2, sp.gy, storage, REG ? 0 : 1, stats, s);
+        else lbm_step_kernel<S, REG, FORCE><<<dim3(sp.gx, sp.gy), block, 0, s>>>(ai);
     }
 }
 
 template <typename S, bool REG>
 static void launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaStream_t s, cudaStream_t side)
 {
-    const Split sp = split_of(a0.nx, a0.ny, a0.nz, a0.interior, VecOf<S>::CPL);
+    const Split sp = split_of(a0, VecOf<S>::CPL);
     StepArgs a = a0;
-    a.il = sp.il;
-    a.ir = sp.ir;
-    const bool tma = use_tma(a, sp, tmap) && tma_usable(a.nx, sizeof(S) == 4 ? 0 : 1);
-    a.total_blocks = (unsigned)(sp.n_edge + (tma ? (sp.ir - sp.il) / 2 : sp.gx) * sp.gy);
+    a.bump_t = 0;
     if (a.has_force) launch_forced<S, REG, true>(a, sp, stats, tmap, s, side);
     else launch_forced<S, REG, false>(a, sp, stats, tmap, s, side);
 }
 
-// One fused step pass.  With a side stream and two events the edge columns
-// run on a forked branch concurrently with the interior columns (both read
-// only the previous lattice and write disjoint cells); `s` waits for both.
+// One fused step pass.  With a side stream and two events the edge work runs
+// on a forked branch concurrently with the interior (both read only the
+// previous lattice and write disjoint cells); `s` waits for both.
 cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, const void *tmap,
                         cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
 {
