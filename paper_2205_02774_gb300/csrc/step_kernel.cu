@@ -434,12 +434,14 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
 
 // Vector kernel over all x of rows 1..ny-2 (YEDGE false) or of rows 0 and
 // ny-1 (YEDGE true; that launch also advances the device step counter).  The
+// regularized plain-step variants fit 64 registers (4 blocks, 32 warps per
+// SM); BGK and sampling variants get 80.  The
 // warps of a block are 8 z-lanes of one CPL*32-wide x chunk.  STATS is chosen
 // on the host (it knows the step count): the sampling-step variant is a
 // separate instantiation, so the plain z loop keeps its registers free of the
 // statistics bookkeeping.
 template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE>
-__global__ void __launch_bounds__(BX *BZ, VecOf<S>::CPL == 2 ? 3 : 2) lbm_vec_kernel(const StepArgs a)
+__global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kernel(const StepArgs a)
 {
     constexpr int CPL = VecOf<S>::CPL;
     __shared__ float sacc[STATS ? BZ : 1][9][BX * CPL];  // per-thread statistics slots
