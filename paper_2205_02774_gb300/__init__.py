@@ -12,7 +12,7 @@ from .capi import lib, StgError  # noqa: F401
 
 
 def build(force=False):
-    from .build import build as _b
+    from .compile_lib import build as _b
     return _b(force=force)
 
 
