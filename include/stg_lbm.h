@@ -203,6 +203,31 @@ int stg_mode_draws(uint64_t seed, int32_t n, double *out);
 /* Library version string. */
 const char *stg_lbm_version(void);
 
+/* FP64 mass (sum over cells and populations of f_i) of a stored population
+ * field, for callers that cannot allocate device memory: code running where
+ * cudaMalloc is forbidden or too costly (a fixed device-memory budget that is
+ * already committed, a latency-critical loop where an allocation would
+ * synchronise the device, or a host framework that owns every allocation).
+ * The paper has no counterpart; this is the same reduction kernel that
+ * stg_lbm_stats uses, with its scratch in a file-scope device array instead
+ * of handle memory.
+ *   pops      device pointer to 19*nx*ny*nz elements in the storage format
+ *             (g_i = f_i - w_i as float for STG_FP32, as binary16 for
+ *             STG_FP16_SHIFTED), layout f[i][z][y][x];
+ *   mass_out  device pointer to one double, written when the kernel finishes;
+ *   stream    cudaStream_t the work is ordered on (NULL: legacy stream).
+ * Allocates nothing (no cudaMalloc/cudaFree, no allocating library routine).
+ * The scratch is 8 KB per GPU that loads the library, held until process
+ * exit, shared by every call on that GPU: calls that overlap on the GPU race,
+ * and each call clears the counter it needs before launching.  The first call
+ * on a device (with that device current) looks up the scratch address with
+ * cudaGetSymbolAddress: make that first call before any stream capture.
+ * At most 2^31-1 cells; larger sizes, NULL pointers or a bad storage code
+ * return STG_ERR_INVALID, CUDA failures STG_ERR_CUDA (message via
+ * stg_lbm_last_error(NULL)).  Asynchronous: returns after enqueueing. */
+int stg_lattice_mass_noalloc(const void *pops, int32_t storage, int32_t nx, int32_t ny, int32_t nz,
+                             double *mass_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

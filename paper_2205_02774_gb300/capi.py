@@ -76,6 +76,8 @@ _SIGNATURES = {
     "stg_lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "stg_mode_draws": (C.c_int, [C.c_uint64, C.c_int32, c_double_p]),
     "stg_lbm_version": (C.c_char_p, []),
+    "stg_lattice_mass_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                           C.c_void_p]),
 }
 
 _lib = None
@@ -181,3 +183,10 @@ def stg_mode_draws(seed, n):
 
 def stg_lbm_version():
     return lib().stg_lbm_version().decode()
+
+
+def stg_lattice_mass_noalloc(pops_dev, storage, nx, ny, nz, mass_out_dev, stream=0):
+    """Enqueue the FP64 mass of a device population field into mass_out_dev
+    (a device double) without any allocation; returns the status code."""
+    return lib().stg_lattice_mass_noalloc(C.c_void_p(pops_dev), storage, nx, ny, nz, C.c_void_p(mass_out_dev),
+                                          C.c_void_p(stream))

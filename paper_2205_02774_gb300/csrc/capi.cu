@@ -26,6 +26,11 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+namespace stg {
+// message for stg_lbm_last_error(NULL) from entry points without a handle
+void record_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace stg
+
 struct stg_lbm {
     stg_domain d{};
     stg_params p{};
