@@ -133,6 +133,32 @@ def _dist():
     return ws, rank, local
 
 
+def rank_seed(base, rank):
+    """Each rank runs its own channel: the STG seed is offset by the rank."""
+    return base + rank
+
+
+def aggregate_ranks(ms_local, cells_per_rank, steps, dist=None, device="cpu"):
+    """Whole-job throughput over the ranks: the timed region is the maximum
+    of the ranks' times, the work is the sum of their cell updates.  Returns
+    (ms_max, MLUPS)."""
+    import torch
+    ws = 1
+    ms = float(ms_local)
+    cells = float(cells_per_rank)
+    if dist is not None and dist.is_initialized():
+        ws = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        w = torch.tensor([cells], dtype=torch.float64, device=device)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+        cells = float(w.item())
+    else:
+        cells = cells * ws
+    return ms, cells * steps / (ms * 1e-3) / 1e6
+
+
 def cpu_baseline(workload, storage, steps):
     """The CPU FP64 oracle, as it stands, on a bounded sample of the workload."""
     import oracle
@@ -195,7 +221,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     c = case(args.workload).with_(storage=args.storage)
-    ch = Channel.from_case(c, check_every=100, mass_tol=0.5, seed=c.seed + rank)
+    ch = Channel.from_case(c, check_every=100, mass_tol=0.5, seed=rank_seed(c.seed, rank))
     stream = ch.stream
 
     # warm-up (also initialises graphs, clocks)
@@ -220,11 +246,7 @@ def run_ours(args):
     e1.synchronize()
     barrier()
     clocks = sampler.stop() if sampler else None
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = aggregate_ranks(e0.elapsed_time(e1), c.cells, args.steps, dist, device="cuda")
     st = ch.stats()
     if st["rc"] != 0:
         raise RuntimeError(f"channel check failed: {st['error']}")
@@ -261,7 +283,6 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     bpc = BYTES_PER_CELL[args.storage]
     achieved = bpc * c.cells / (ms_step * 1e-3) / 1e9
-    value = c.cells * args.steps * ws / (ms * 1e-3) / 1e6
     traffic = _traffic(args.workload, args.storage)
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
