@@ -175,9 +175,11 @@ def cpu_baseline(workload, storage, steps):
 
 def run_reference(args):
     """Reference arm: the CPU FP64 oracle on the host cores.  Each step is one
-    oracle step of a bounded slab of the workload (same ny x nz cross-section,
-    inlet, outlet and walls; nx chosen so that warm-up + timed steps stay
-    within about a minute of CPU time)."""
+    oracle step of a bounded sample of the workload: the full streamwise
+    length and span (so the share of inlet-generator work per cell, N / nx,
+    and the OpenMP split over z are those of the full channel) with fewer
+    wall-normal rows (at least 2, walls on both), chosen so that warm-up +
+    timed steps stay within about a minute of CPU time."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
@@ -185,15 +187,15 @@ def run_reference(args):
     from workloads import case
     full = case(args.workload)
     budget_cells = 3.0e8  # cell updates over the whole run
-    nx = max(3, min(full.nx, int(budget_cells / ((args.steps + args.warmup) * full.ny * full.nz))))
-    c = full.with_(nx=nx)
+    ny = max(2, min(full.ny, int(budget_cells / ((args.steps + args.warmup) * full.nx * full.nz))))
+    c = full.with_(ny=ny)
     sim = oracle.Sim.from_case(c)
     sim.step(args.warmup)
     t0 = time.perf_counter()
     sim.step(args.steps)
     t = time.perf_counter() - t0
     value = c.cells * args.steps / t / 1e6
-    sample = (f"{args.steps} timed steps (+{args.warmup} warm-up) of a {nx}x{c.ny}x{c.nz} slab of the "
+    sample = (f"{args.steps} timed steps (+{args.warmup} warm-up) of a {c.nx}x{ny}x{c.nz} slice of the "
               f"{args.workload} channel (inlet, outlet, walls, {c.n_modes} STG modes)")
     line = {"impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
