@@ -190,6 +190,38 @@ int stg_lbm_device_state(stg_lbm *h, void **pops, float **inlet_u);
 
 int stg_lbm_info(const stg_lbm *h, stg_info *out);
 
+/* Launch tile of the plain (non-sampling) steps of the vector step kernels
+ * (lattices with even nx; other lattices ignore it).  The paper fixes no
+ * kernel decomposition: the tile changes only how the lattice is cut into
+ * thread blocks, never the arithmetic of a cell, so every tile gives
+ * bit-identical populations and statistics (the FP64 mass of a check can
+ * differ in its last bits, its block partials being summed in another order).
+ *   interior_layout  0: 8 warps on one 64-cell x chunk, warps interleaved in z;
+ *                    1: 4 warps on 4 consecutive 64-cell x chunks walking z together
+ *   interior_zc      z planes per block of the rows 1..ny-2 (0: the whole z column,
+ *                    else >= 4)
+ *   wall_zc          z planes per block of the wall rows y = 0, ny-1 (0 or >= 4)
+ * Default {1, 8, 24}. */
+typedef struct {
+    int32_t interior_layout;
+    int32_t interior_zc;
+    int32_t wall_zc;
+    int32_t pad0;
+} stg_tile;
+
+/* Set the tile (re-captures the step graphs; synchronises the stream).
+ * Errors: STG_ERR_INVALID (bad field; the tile is unchanged), STG_ERR_CUDA. */
+int stg_lbm_set_tile(stg_lbm *h, const stg_tile *tile);
+int stg_lbm_get_tile(const stg_lbm *h, stg_tile *tile);
+
+/* Autotuner: time every candidate tile on this lattice (`trial_passes` >= 1
+ * plain step passes each, CUDA events on the handle's stream, after one
+ * warm-up pass), keep the fastest and store it in *chosen (may be NULL).
+ * The trial passes recompute the next state from the current one without
+ * advancing the step counter, the inlet filter or the statistics, so tuning
+ * leaves the simulation's results unchanged.  Synchronises the stream. */
+int stg_lbm_autotune(stg_lbm *h, int32_t trial_passes, stg_tile *chosen);
+
 /* Release everything the handle owns (NULL-safe).  Synchronises its stream. */
 void stg_lbm_destroy(stg_lbm *h);
 

@@ -42,6 +42,11 @@ class stg_params(C.Structure):
                 ("T_filter", C.c_double)]
 
 
+class stg_tile(C.Structure):
+    _fields_ = [("interior_layout", C.c_int32), ("interior_zc", C.c_int32), ("wall_zc", C.c_int32),
+                ("pad0", C.c_int32)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 
@@ -72,6 +77,9 @@ _SIGNATURES = {
     "stg_lbm_get_inlet": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
     "stg_lbm_device_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
     "stg_lbm_info": (C.c_int, [C.c_void_p, C.POINTER(stg_info)]),
+    "stg_lbm_set_tile": (C.c_int, [C.c_void_p, C.POINTER(stg_tile)]),
+    "stg_lbm_get_tile": (C.c_int, [C.c_void_p, C.POINTER(stg_tile)]),
+    "stg_lbm_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(stg_tile)]),
     "stg_lbm_destroy": (None, [C.c_void_p]),
     "stg_lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "stg_mode_draws": (C.c_int, [C.c_uint64, C.c_int32, c_double_p]),
@@ -164,6 +172,23 @@ def stg_lbm_info(h):
     i = stg_info()
     _check(lib().stg_lbm_info(h, C.byref(i)), h)
     return i
+
+
+def stg_lbm_set_tile(h, layout, zc, wall_zc):
+    t = stg_tile(layout, zc, wall_zc, 0)
+    return _check(lib().stg_lbm_set_tile(h, C.byref(t)), h)
+
+
+def stg_lbm_get_tile(h):
+    t = stg_tile()
+    _check(lib().stg_lbm_get_tile(h, C.byref(t)), h)
+    return t.interior_layout, t.interior_zc, t.wall_zc
+
+
+def stg_lbm_autotune(h, trial_passes=10):
+    t = stg_tile()
+    _check(lib().stg_lbm_autotune(h, trial_passes, C.byref(t)), h)
+    return t.interior_layout, t.interior_zc, t.wall_zc
 
 
 def stg_lbm_destroy(h):

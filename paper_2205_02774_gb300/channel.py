@@ -114,6 +114,15 @@ class Channel:
     def step(self, n=1):
         A.stg_lbm_step(self.h, n)
 
+    def set_tile(self, layout, zc, wall_zc):
+        A.stg_lbm_set_tile(self.h, layout, zc, wall_zc)
+
+    def tile(self):
+        return A.stg_lbm_get_tile(self.h)
+
+    def autotune(self, trial_passes=10):
+        return A.stg_lbm_autotune(self.h, trial_passes)
+
     def step_timed(self, n):
         return A.stg_lbm_step_timed(self.h, n)
 

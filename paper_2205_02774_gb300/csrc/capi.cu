@@ -13,8 +13,7 @@
 #include <vector>
 
 #include "d3q19.cuh"
-#include "internal.h"
-#include "stg_lbm.h"
+#include "handle.h"
 
 using stg::StepCtl;
 
@@ -31,51 +30,8 @@ namespace stg {
 void record_error(const std::string &msg) { g_create_error = msg; }
 }  // namespace stg
 
-struct stg_lbm {
-    stg_domain d{};
-    stg_params p{};
-    bool inout = false;
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    stg_allocator alloc{};
-    bool has_alloc = false;
-    std::vector<std::pair<void *, size_t>> allocs;
-    size_t P = 0, elem = 4;
-    void *lat[2] = {nullptr, nullptr};
-    float *ubc = nullptr, *uf = nullptr;
-    float *A = nullptr, *B = nullptr, *SQ = nullptr, *sig = nullptr, *a6 = nullptr, *u_int = nullptr;
-    double *phi = nullptr, *omg = nullptr;
-    int N = 0;
-    float a_filter = 0.f;
-    StepCtl *ctl = nullptr;
-    double *stat_mean = nullptr, *stat_rey = nullptr;
-    double *mass_partial = nullptr, *mass_out = nullptr;
-    unsigned *mass_counter = nullptr;
-    double *m_partial = nullptr, *m_out = nullptr;
-    unsigned *m_counter = nullptr;
-    double *h_pinned = nullptr;  // [0]: last checked mass
-    cudaEvent_t ev_check = nullptr, ev_done = nullptr;
-    cudaStream_t side = nullptr;                       // branch for the edge kernel
-    alignas(64) unsigned char tmap[2][128];            // tensor maps of the two lattices (CUtensorMap)
-    bool has_tmap = false;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    bool check_pending = false;
-    int64_t t = 0, t0_stats = 0;
-    double mass0 = 0.0;
-    int sticky = STG_OK;
-    std::string err;
-    // single steps by [parity][sampling step]; blocks of block_steps steps that
-    // start at a step index divisible by the sampling period, by parity
-    cudaGraphExec_t g_single[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    cudaGraphExec_t g_block[2] = {nullptr, nullptr};
-    int block_steps = 16;
-    stg_info info{};
-    double timeout_s = 900.0;
-    int interior = 0;  // STG_LBM_INTERIOR=scalar|pair|tma overrides the interior kernel choice
-};
-
-namespace {
+namespace stg {
+namespace host {
 
 int fail(stg_lbm *h, int code, const std::string &msg)
 {
@@ -88,6 +44,13 @@ int cuda_fail(stg_lbm *h, cudaError_t e, const char *what)
 {
     return fail(h, STG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+}  // namespace host
+}  // namespace stg
+
+using namespace stg::host;
+
+namespace {
 
 #define CK(call)                                                \
     do {                                                        \
@@ -320,6 +283,9 @@ stg::StepArgs step_args(const stg_lbm *h, int parity)
     a.parity = parity;
     a.stats_every = h->d.stats_every;
     a.interior = h->interior;
+    a.tile_layout = h->tile.interior_layout;
+    a.tile_zc = h->tile.interior_zc;
+    a.tile_wall_zc = h->tile.wall_zc;
     a.check_every = h->d.check_every;
     a.stat_mean = h->stat_mean;
     a.stat_rey = h->stat_rey;
@@ -351,13 +317,28 @@ stg::InletArgs inlet_args(const stg_lbm *h, int parity)
     return a;
 }
 
+}  // namespace
+
+namespace stg {
+namespace host {
+
 bool is_stats_step(const stg_lbm *h, int64_t t)
 {
     return h->d.stats_every > 0 && (t + 1) % h->d.stats_every == 0;
 }
 
+}  // namespace host
+}  // namespace stg
+
+namespace {
+
 // one step with the given parity (the device reads the step index itself);
 // `stats` selects the sampling-step kernel variant
+}  // namespace
+
+namespace stg {
+namespace host {
+
 cudaError_t enqueue_step(stg_lbm *h, int parity, bool stats)
 {
     cudaError_t e = cudaSuccess;
@@ -368,6 +349,11 @@ cudaError_t enqueue_step(stg_lbm *h, int parity, bool stats)
     return stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, stats,
                             h->has_tmap ? h->tmap[parity] : nullptr, h->stream, h->side, h->ev_fork, h->ev_join);
 }
+
+}  // namespace host
+}  // namespace stg
+
+namespace {
 
 // Graph of `steps` steps starting with parity p0.  single_stats >= 0: one
 // step with that sampling flag; otherwise step s samples when (s + 1) is a
@@ -391,6 +377,42 @@ int capture(stg_lbm *h, int p0, int steps, int single_stats, cudaGraphExec_t *ou
     return STG_OK;
 }
 
+void destroy_graphs(stg_lbm *h)
+{
+    for (int p = 0; p < 2; ++p) {
+        for (int q = 0; q < 2; ++q) {
+            if (h->g_single[p][q]) cudaGraphExecDestroy(h->g_single[p][q]);
+            h->g_single[p][q] = nullptr;
+        }
+        if (h->g_block[p]) cudaGraphExecDestroy(h->g_block[p]);
+        h->g_block[p] = nullptr;
+    }
+}
+
+// Single-step graphs by [parity][sampling] and the block graphs by parity.
+int capture_all(stg_lbm *h)
+{
+    destroy_graphs(h);
+    int rc = STG_OK;
+    for (int p = 0; p < 2 && rc == STG_OK; ++p) {
+        rc = capture(h, p, 1, 0, &h->g_single[p][0]);
+        if (rc == STG_OK && h->d.stats_every > 0) rc = capture(h, p, 1, 1, &h->g_single[p][1]);
+        if (rc == STG_OK && h->block_steps > 0) rc = capture(h, p, h->block_steps, -1, &h->g_block[p]);
+    }
+    return rc;
+}
+
+bool tile_ok(const stg_tile &t)
+{
+    return (t.interior_layout == 0 || t.interior_layout == 1) &&
+           (t.interior_zc == 0 || t.interior_zc >= stg::MIN_ZC) && (t.wall_zc == 0 || t.wall_zc >= stg::MIN_ZC);
+}
+
+}  // namespace
+
+namespace stg {
+namespace host {
+
 int wait_stream(stg_lbm *h)
 {
     CK(cudaEventRecord(h->ev_done, h->stream));
@@ -405,7 +427,17 @@ int wait_stream(stg_lbm *h)
     }
 }
 
+}  // namespace host
+}  // namespace stg
+
+namespace {
+
 // Evaluate the last completed mass check (non-blocking).
+}  // namespace
+
+namespace stg {
+namespace host {
+
 int poll_check(stg_lbm *h)
 {
     if (!h->check_pending) return STG_OK;
@@ -426,6 +458,33 @@ int poll_check(stg_lbm *h)
     }
     return STG_OK;
 }
+
+}  // namespace host
+}  // namespace stg
+
+namespace {
+
+}  // namespace
+
+namespace stg {
+namespace host {
+
+int queue_check_readback(stg_lbm *h, int64_t t_before)
+{
+    (void)t_before;
+    // read back the last check only once a check step has run since the reset
+    if (h->d.check_every > 0 && h->t / h->d.check_every > h->t0_stats / h->d.check_every) {
+        CK(cudaMemcpyAsync(h->h_pinned, h->mass_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaEventRecord(h->ev_check, h->stream));
+        h->check_pending = true;
+    }
+    return STG_OK;
+}
+
+}  // namespace host
+}  // namespace stg
+
+namespace {
 
 int compute_mass(stg_lbm *h, double *out)
 {
@@ -467,11 +526,7 @@ void release(stg_lbm *h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    for (int p = 0; p < 2; ++p) {
-        for (int q = 0; q < 2; ++q)
-            if (h->g_single[p][q]) cudaGraphExecDestroy(h->g_single[p][q]);
-        if (h->g_block[p]) cudaGraphExecDestroy(h->g_block[p]);
-    }
+    destroy_graphs(h);
     for (auto &a : h->allocs) {
         if (h->has_alloc) h->alloc.free(a.first, a.second, h->alloc.ctx);
         else cudaFree(a.first);
@@ -587,7 +642,7 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
     h->ctl = (StepCtl *)dalloc(h, sizeof(StepCtl));
     h->stat_mean = (double *)dalloc(h, sizeof(double) * 3 * (size_t)nx * ny);
     h->stat_rey = (double *)dalloc(h, sizeof(double) * 6 * (size_t)nx * ny);
-    h->mass_partial = (double *)dalloc(h, sizeof(double) * stg::step_grid_blocks(nx, ny));
+    h->mass_partial = (double *)dalloc(h, sizeof(double) * stg::step_grid_blocks(nx, ny, nz));
     h->mass_counter = (unsigned *)dalloc(h, sizeof(unsigned) * 4);
     h->mass_out = (double *)dalloc(h, sizeof(double) * 2);
     h->m_partial = (double *)dalloc(h, sizeof(double) * stg::mass_grid_blocks());
@@ -635,11 +690,7 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
     const int k = domain->stats_every;
     h->block_steps = k > 0 ? k * ((16 + k - 1) / k) : 16;
     if (h->block_steps > 256) h->block_steps = 0;  // very long sampling periods: single-step graphs only
-    for (int p = 0; p < 2 && rc == STG_OK; ++p) {
-        rc = capture(h, p, 1, 0, &h->g_single[p][0]);
-        if (rc == STG_OK && k > 0) rc = capture(h, p, 1, 1, &h->g_single[p][1]);
-        if (rc == STG_OK && h->block_steps > 0) rc = capture(h, p, h->block_steps, -1, &h->g_block[p]);
-    }
+    rc = capture_all(h);
     if (rc) return bail(rc);
     *out = h;
     return STG_OK;
@@ -668,13 +719,7 @@ int stg_lbm_step(stg_lbm *h, int64_t n)
         h->t += k;
         n -= k;
     }
-    // read back the last check only once a check step has run since the reset
-    if (h->d.check_every > 0 && h->t / h->d.check_every > h->t0_stats / h->d.check_every) {
-        CK(cudaMemcpyAsync(h->h_pinned, h->mass_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaEventRecord(h->ev_check, h->stream));
-        h->check_pending = true;
-    }
-    return STG_OK;
+    return queue_check_readback(h, h->t);
 }
 
 int stg_lbm_step_timed(stg_lbm *h, int64_t n, double *ms_step, double *ms_inlet)
@@ -794,6 +839,84 @@ int stg_lbm_info(const stg_lbm *h, stg_info *out)
     if (!h || !out) return STG_ERR_INVALID;
     *out = h->info;
     return STG_OK;
+}
+
+int stg_lbm_set_tile(stg_lbm *h, const stg_tile *tile)
+{
+    if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
+    if (!tile || !tile_ok(*tile)) return fail(h, STG_ERR_INVALID, "tile: layout 0 or 1, z chunks 0 or >= 4");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    const stg_tile old = h->tile;
+    h->tile = *tile;
+    h->tile.pad0 = 0;
+    rc = capture_all(h);
+    if (rc) {
+        h->tile = old;
+        capture_all(h);
+    }
+    return rc;
+}
+
+int stg_lbm_get_tile(const stg_lbm *h, stg_tile *tile)
+{
+    if (!h || !tile) return STG_ERR_INVALID;
+    *tile = h->tile;
+    return STG_OK;
+}
+
+int stg_lbm_autotune(stg_lbm *h, int32_t trial_passes, stg_tile *chosen)
+{
+    if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
+    if (trial_passes < 1 || trial_passes > 1000) return fail(h, STG_ERR_INVALID, "trial_passes must be in [1, 1000]");
+    if (h->sticky) return fail(h, h->sticky, "an earlier check failed; reset the state first");
+    static const stg_tile cand[] = {{1, 4, 24, 0},  {1, 6, 24, 0},  {1, 8, 24, 0},  {1, 12, 24, 0}, {1, 16, 24, 0},
+                                    {1, 8, 8, 0},   {0, 16, 24, 0}, {0, 24, 24, 0}, {0, 48, 24, 0}, {0, 0, 0, 0}};
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(h, STG_ERR_CUDA, "cudaEventCreate");
+    }
+    // plain passes from the current state: src = lat[t & 1], dst = lat[(t & 1) ^ 1];
+    // the pass writes the device counter t[p ^ 1] = t + 1, which the next real
+    // step writes again, and the mass slots, which every pass rewrites
+    const int parity = (int)(h->t & 1);
+    const stg_tile keep = h->tile;
+    stg_tile best = keep;
+    float best_ms = -1.f;
+    for (const stg_tile &c : cand) {
+        h->tile = c;
+        stg::StepArgs a = step_args(h, parity);
+        a.stats_every = 0;  // the boundary kernel samples on its own otherwise
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k <= trial_passes && e == cudaSuccess; ++k) {
+            if (k == 1) e = cudaEventRecord(e0, h->stream);
+            if (e == cudaSuccess)
+                e = stg::launch_step(a, h->d.storage, h->d.collision, false, h->has_tmap ? h->tmap[parity] : nullptr,
+                                     h->stream, h->side, h->ev_fork, h->ev_join);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(h, e, "autotune pass");
+            break;
+        }
+        if (best_ms < 0.f || ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->tile = keep;
+    if (rc) return rc;
+    rc = stg_lbm_set_tile(h, &best);
+    if (rc == STG_OK && chosen) *chosen = best;
+    return rc;
 }
 
 void stg_lbm_destroy(stg_lbm *h) { release(h); }

@@ -31,6 +31,10 @@ struct StepArgs {
     void *dstp[19];
     int il, ir;             // 32-wide x chunks [il, ir) of rows 1..ny-2 belong to the interior kernel
     int interior;           // interior kernel: 0 best available, 1 one cell per thread, 2 cell pairs, 3 TMA-staged
+    // tile of the plain (non-sampling) vector launches: layout 0 = 8 z-warps on one 64-cell x chunk,
+    // layout 1 = 4 x-warps (256 cells) walking z together; zc / wall_zc = z planes per block of the
+    // rows 1..ny-2 / wall-row launch (0: the whole z column)
+    int tile_layout, tile_zc, tile_wall_zc;
     unsigned total_blocks;  // blocks of all step kernels of the pass (mass-check completion count)
     int slot_base;          // first mass-partial slot of this launch's blocks
     int bump_t;             // this launch advances the device step counter
@@ -102,7 +106,10 @@ int tma_encode(void *map_out, const void *lattice, int storage, int nx, int ny, 
 cudaError_t launch_tma(const StepArgs &a, const void *tensor_map, int gx, int gy, int storage, int collision,
                        bool stats, cudaStream_t s);
 
-int step_grid_blocks(int nx, int ny);
+// Upper bound of the mass-partial slots of one step pass over every tile
+// that set_tile accepts (z chunks of at least MIN_ZC planes).
+constexpr int MIN_ZC = 4;
+int step_grid_blocks(int nx, int ny, int nz);
 int mass_grid_blocks();
 
 }  // namespace stg

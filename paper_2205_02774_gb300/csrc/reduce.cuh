@@ -6,7 +6,8 @@
 namespace stg {
 
 // Deterministic FP64 mass of a step pass: each block leaves the sum of its
-// threads' (rho - 1) in its own slot, a.slot_base + its linear block index;
+// threads' (rho - 1) in its own slot, a.slot_base + its linear block index
+// (x fastest, then y, then z);
 // the last of all total_blocks blocks of the pass (all kernels) adds the
 // slots in index order and writes nx ny nz + sum.  NT = threads per block (a
 // power of two, at most 256).
@@ -23,7 +24,7 @@ __device__ __forceinline__ void mass_finish(const StepArgs &a, float sdr)
         __syncthreads();
     }
     if (tid == 0) {
-        a.mass_partial[a.slot_base + blockIdx.y * gridDim.x + blockIdx.x] = rd[0];
+        a.mass_partial[a.slot_base + (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = rd[0];
         __threadfence();
         const unsigned prev = atomicAdd(a.mass_counter, 1u);
         s_last = (prev == a.total_blocks - 1);

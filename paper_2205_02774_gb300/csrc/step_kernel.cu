@@ -316,7 +316,8 @@ struct VecOf {
     static constexpr int CPL = 2;
 };
 
-// One vector column (CPL 32 cells wide) at row y over all z.  YEDGE rows
+// One vector column (CPL 32 cells wide) at row y over the planes z = zb,
+// zb + zs, ... below ze.  YEDGE rows
 // (y = 0 or ny-1) take the y neighbour by half-way bounce-back (walls: the
 // cell's own opposite population) or by the periodic wrap.  In inlet/outlet
 // mode the cells x = 0 and x = nx-1 are left to the boundary kernel: their
@@ -324,7 +325,8 @@ struct VecOf {
 // per-cell velocity sums to the block's shared-memory slots.  Returns the
 // thread's sum of rho - 1.
 template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE>
-__device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX * VecOf<S>::CPL], int x0, int y)
+__device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX * VecOf<S>::CPL], int x0, int y,
+                                          int zb, int ze, int zs)
 {
     constexpr int CPL = VecOf<S>::CPL;
     using V = Vec<S, CPL>;
@@ -336,7 +338,7 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
     const bool active = x < nx;
     const bool inout = a.bc_x == 0;
     // x halo read directly by lane 0 / by the last active lane
-    const bool side_l = lane == 0;
+    const bool side_l = active && lane == 0;
     const bool side_r = active && (lane == 31 || x + CPL == nx);
     const int xl = x == 0 ? (inout ? 0 : nx - 1) : x - 1;        // element read for x-1
     const int xr = x + CPL == nx ? (inout ? nx - 1 : 0) : x + CPL; // element read for x+CPL
@@ -362,7 +364,7 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
     const S *__restrict__ sbase = static_cast<const S *>(a.src);
     S *__restrict__ dbase = static_cast<S *>(a.dst);
     float sdr = 0.f;
-    for (int z = wi; z < nz; z += BZ) {
+    for (int z = zb; z < ze; z += zs) {
         // Plane offsets i P are recomputed in every iteration from an opaque
         // copy of P: hoisting 19 + 19 plane pointers out of the loop would
         // cost 76 registers.  Element offsets are 32-bit (19 P < 2^32).
@@ -432,14 +434,12 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
     return sdr;
 }
 
-// Vector kernel over all x of rows 1..ny-2 (YEDGE false) or of rows 0 and
-// ny-1 (YEDGE true; that launch also advances the device step counter).  The
-// regularized plain-step variants fit 64 registers (4 blocks, 32 warps per
-// SM); BGK and sampling variants get 80.  The
-// warps of a block are 8 z-lanes of one CPL*32-wide x chunk.  STATS is chosen
-// on the host (it knows the step count): the sampling-step variant is a
-// separate instantiation, so the plain z loop keeps its registers free of the
-// statistics bookkeeping.
+// Sampling-step vector kernel over all x of rows 1..ny-2 (YEDGE false) or of
+// rows 0 and ny-1 (YEDGE true; that launch also advances the device step
+// counter).  The warps of a block are 8 z-lanes of one CPL*32-wide x chunk and
+// the block walks the whole z column, so the per-(x, y) statistics are summed
+// in shared memory without atomics and in a fixed order.  STATS is chosen on
+// the host (it knows the step count); plain steps use lbm_vec_zc_kernel.
 template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE>
 __global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kernel(const StepArgs a)
 {
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kerne
 #pragma unroll
             for (int j = 0; j < CPL; ++j) sacc[wi][q][CPL * lane + j] = 0.f;
     }
-    const float sdr = vec_loop<S, REG, FORCE, STATS, YEDGE>(a, sacc, x0, y);
+    const float sdr = vec_loop<S, REG, FORCE, STATS, YEDGE>(a, sacc, x0, y, wi, a.nz, BZ);
     if (STATS) {
         __syncthreads();
         if (wi == 0) {
@@ -480,6 +480,41 @@ __global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kerne
     }
     if (do_check) mass_finish<BX * BZ>(a, sdr);
     if (YEDGE && a.bump_t && blockIdx.x == 0 && blockIdx.y == 0 && lane == 0 && wi == 0)
+        a.ctl->t[a.parity ^ 1] = t + 1;
+}
+
+// Plain-step vector kernel, tiled in z: block (x chunk, row, z chunk of
+// a.tile_zc planes, or of a.tile_wall_zc planes for the wall rows).  Many
+// short blocks instead of one block per z column keep the last wave of the
+// grid small.  LAYOUT 0: 8 warps on one 64-cell x chunk, warp w taking the
+// planes w, w + 8, ... of the chunk; LAYOUT 1: 4 warps on 4 consecutive x
+// chunks (256 cells), all walking the chunk's planes together.  The regularized
+// unforced variants fit 64 registers (32 warps per SM); BGK and forced ones
+// get 80 (24 warps per SM).
+template <int LAYOUT, bool LEAN>
+struct ZcShape {
+    static constexpr int NW = LAYOUT == 0 ? BZ : 4;  // warps per block
+    static constexpr int MINB = (LEAN ? 32 : 24) / NW;  // resident blocks per SM
+};
+
+template <typename S, bool REG, bool FORCE, int LAYOUT, bool YEDGE>
+__global__ void __launch_bounds__(BX *ZcShape<LAYOUT, REG && !FORCE>::NW, ZcShape<LAYOUT, REG && !FORCE>::MINB)
+    lbm_vec_zc_kernel(const StepArgs a)
+{
+    constexpr int CPL = VecOf<S>::CPL;
+    constexpr int NW = ZcShape<LAYOUT, REG && !FORCE>::NW;
+    const int wi = threadIdx.y;
+    const int y = YEDGE ? (blockIdx.y == 0 ? 0 : a.ny - 1) : blockIdx.y + 1;
+    const int zc0 = YEDGE ? a.tile_wall_zc : a.tile_zc;
+    const int zc = zc0 > 0 ? zc0 : a.nz;
+    const int zb = blockIdx.z * zc, ze = min(zb + zc, a.nz);
+    const long long t = a.ctl->t[a.parity];
+    const bool do_check = a.check_every > 0 && ((t + 1) % a.check_every) == 0;
+    float sdr;
+    if (LAYOUT == 0) sdr = vec_loop<S, REG, FORCE, false, YEDGE>(a, nullptr, BX * CPL * blockIdx.x, y, zb + wi, ze, NW);
+    else sdr = vec_loop<S, REG, FORCE, false, YEDGE>(a, nullptr, BX * CPL * (NW * blockIdx.x + wi), y, zb, ze, 1);
+    if (do_check) mass_finish<BX * NW>(a, sdr);
+    if (YEDGE && a.bump_t && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && wi == 0)
         a.ctl->t[a.parity ^ 1] = t + 1;
 }
 
@@ -601,8 +636,12 @@ __global__ void __launch_bounds__(BX *BZ, 2) lbm_edge_kernel(const StepArgs a)
     if (a.bump_t && b == 0 && threadIdx.x == 0 && threadIdx.y == 0) a.ctl->t[a.parity ^ 1] = t + 1;
 }
 
-// Upper bound of the mass-partial slots a step pass uses (one per block).
-int step_grid_blocks(int nx, int ny) { return ((nx + BX - 1) / BX) * ny + 2 * ny + 64; }
+int step_grid_blocks(int nx, int ny, int nz)
+{
+    const long long vec = (long long)((nx + 2 * BX - 1) / (2 * BX)) * ny * ((nz + MIN_ZC - 1) / MIN_ZC);
+    const long long col = (long long)((nx + BX - 1) / BX) * ny;
+    return (int)((vec > col ? vec : col) + 2LL * ny + 64);
+}
 
 // How a pass covers the lattice.
 //  vector split: vector kernel on rows 1..ny-2 and on rows {0, ny-1} (all x),
@@ -646,9 +685,27 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
     const dim3 block(BX, BZ);
     const int storage = sizeof(S) == 4 ? 0 : 1;
     if (sp.vec) {
-        const int ny = a.ny;
+        constexpr int cpl = VecOf<S>::CPL;
+        const int nx = a.nx, ny = a.ny;
         const int rows_in = ny > 2 ? ny - 2 : 0, rows_edge = ny >= 2 ? 2 : 1;
-        const int n_in = sp.nxv * rows_in, n_edge = sp.nxv * rows_edge;
+        const int nz = a.nz;
+        // grids: sampling steps take whole z columns (statistics summed per
+        // block); plain steps take the tile's z chunks
+        dim3 gi(sp.nxv, rows_in), ge(sp.nxv, rows_edge);
+        dim3 bi = block;
+        if (!stats) {
+            const int zc = a.tile_zc > 0 ? a.tile_zc : nz, wzc = a.tile_wall_zc > 0 ? a.tile_wall_zc : nz;
+            if (a.tile_layout == 1) {
+                constexpr int W = ZcShape<1, true>::NW;
+                gi = dim3((nx + BX * cpl * W - 1) / (BX * cpl * W), rows_in, (nz + zc - 1) / zc);
+                bi = dim3(BX, W);
+            } else {
+                gi = dim3(sp.nxv, rows_in, (nz + zc - 1) / zc);
+            }
+            ge = dim3(sp.nxv, rows_edge, (nz + wzc - 1) / wzc);
+        }
+        const int n_in = rows_in > 0 ? (int)(gi.x * gi.y * gi.z) : 0;
+        const int n_edge = (int)(ge.x * ge.y * ge.z);
         const int n_xb = a.bc_x == 0 ? 2 * ny : 0;
         a.total_blocks = (unsigned)(n_in + n_edge + n_xb);
         StepArgs ai = a, ae = a, ab = a;
@@ -657,13 +714,12 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
         ab.slot_base = n_in + n_edge;
         ae.bump_t = 1;
         if (n_in > 0) {
-            const dim3 g(sp.nxv, rows_in);
-            if (stats) lbm_vec_kernel<S, REG, FORCE, true, false><<<g, block, 0, s>>>(ai);
-            else lbm_vec_kernel<S, REG, FORCE, false, false><<<g, block, 0, s>>>(ai);
+            if (stats) lbm_vec_kernel<S, REG, FORCE, true, false><<<gi, block, 0, s>>>(ai);
+            else if (a.tile_layout == 1) lbm_vec_zc_kernel<S, REG, FORCE, 1, false><<<gi, bi, 0, s>>>(ai);
+            else lbm_vec_zc_kernel<S, REG, FORCE, 0, false><<<gi, bi, 0, s>>>(ai);
         }
-        const dim3 ge(sp.nxv, rows_edge);
         if (stats) lbm_vec_kernel<S, REG, FORCE, true, true><<<ge, block, 0, side>>>(ae);
-        else lbm_vec_kernel<S, REG, FORCE, false, true><<<ge, block, 0, side>>>(ae);
+        else lbm_vec_zc_kernel<S, REG, FORCE, 0, true><<<ge, block, 0, side>>>(ae);
         if (n_xb > 0) lbm_xbound_kernel<S, REG, FORCE><<<dim3(2, ny), XB_THREADS, 0, side>>>(ab);
         return;
     }
