@@ -24,7 +24,8 @@ class Domain(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("bc_x", C.c_int32), ("bc_y", C.c_int32), ("collision", C.c_int32),
                 ("stats_every", C.c_int32), ("pad0", C.c_int32),
-                ("tau0", C.c_double), ("c_smag", C.c_double), ("force", C.c_double * 3)]
+                ("tau0", C.c_double), ("c_smag", C.c_double), ("force", C.c_double * 3),
+                ("sponge_len", C.c_double), ("sponge_K", C.c_double), ("sponge_p", C.c_double)]
 
 
 class Rans(C.Structure):
@@ -54,6 +55,7 @@ def lib():
             "orc_tau_eff": (C.c_double, [C.c_double, C.c_double, C.c_double, C.c_double]),
             "orc_regularized_neq": (None, [c_double_p, c_double_p]),
             "orc_collide": (None, [C.POINTER(Domain), c_double_p, c_double_p, c_double_p, c_double_p]),
+            "orc_sponge_factor": (C.c_double, [C.POINTER(Domain), C.c_int32]),
             "orc_zou_he_density": (C.c_double, [c_double_p, C.c_double]),
             "orc_inlet_reconstruct": (None, [c_double_p, c_double_p, c_double_p]),
             "orc_outlet_reconstruct": (None, [c_double_p, c_double_p, c_double_p]),
@@ -148,8 +150,10 @@ def regularized_neq(pi):
 
 
 def make_domain(nx, ny, nz, tau0=0.52, c_smag=0.01, force=(0.0, 0.0, 0.0), bc_x="stg",
-                bc_y="walls", collision="regularized", stats_every=0):
+                bc_y="walls", collision="regularized", stats_every=0, sponge=(0.0, 1000.0, 3.0)):
+    """sponge = (length before the outlet column, K, p) of eq. (sponge_visco); length 0: off."""
     d = Domain()
+    d.sponge_len, d.sponge_K, d.sponge_p = sponge
     d.nx, d.ny, d.nz = nx, ny, nz
     d.bc_x = {"stg": 0, "periodic": 1}[bc_x]
     d.bc_y = {"walls": 0, "periodic": 1}[bc_y]
@@ -168,6 +172,11 @@ def collide(f, tau0=0.52, c_smag=0.01, force=(0.0, 0.0, 0.0), collision="regular
     u = np.zeros(3)
     lib().orc_collide(C.byref(d), _dp(f), _dp(out), _dp(rho), _dp(u))
     return out, rho[0], u
+
+
+def sponge_factor(domain, x):
+    """nu_sponge / nu_eff at column x, eq. (sponge_visco)."""
+    return lib().orc_sponge_factor(C.byref(domain), int(x))
 
 
 def zou_he_density(f, ux):
@@ -256,8 +265,9 @@ class Sim:
 
     def __init__(self, nx, ny, nz, tau0=0.52, c_smag=0.01, force=(0.0, 0.0, 0.0), bc_x="stg",
                  bc_y="walls", collision="regularized", stats_every=0, profile=None,
-                 n_modes=100, C_l=3.0, alpha=0.01, t_filter=0.0, mach_target=0.0516, seed=0):
-        self.domain = make_domain(nx, ny, nz, tau0, c_smag, force, bc_x, bc_y, collision, stats_every)
+                 n_modes=100, C_l=3.0, alpha=0.01, t_filter=0.0, mach_target=0.0516, seed=0,
+                 sponge=(0.0, 1000.0, 3.0)):
+        self.domain = make_domain(nx, ny, nz, tau0, c_smag, force, bc_x, bc_y, collision, stats_every, sponge)
         self.nx, self.ny, self.nz = nx, ny, nz
         self._rans = _RansHolder(profile, mach_target) if profile is not None else None
         p = StgParams()
@@ -276,7 +286,8 @@ class Sim:
         args = dict(tau0=case.tau0, c_smag=case.c_smag, force=case.force, bc_x=case.bc_x,
                     bc_y=case.bc_y, collision=case.collision, stats_every=case.stats_every,
                     profile=case.profile() if case.bc_x == "stg" else None, n_modes=case.n_modes,
-                    t_filter=case.t_filter, mach_target=case.mach_target, seed=case.seed)
+                    t_filter=case.t_filter, mach_target=case.mach_target, seed=case.seed,
+                    sponge=(case.sponge_len, case.sponge_K, case.sponge_p))
         args.update(kw)
         return cls(case.nx, case.ny, case.nz, **args)
 

@@ -14,7 +14,8 @@
  *              (psu), (Nmode), (lcut)         -- synthetic turbulence generator
  *   Sec. III.B eqs. (f_i), (f_i_neq), (pi_neq), (unknown_neq), (density_bc),
  *              (density_bc_sub), (bc_eq)      -- regularized inlet reconstruction
- *   Sec. III.C eqs. (u_phys), (u_transfer), (c_factor); Sec. IV eq. (ma-eq)
+ *   Sec. III.C eqs. (u_phys), (u_transfer), (c_factor); Sec. IV eqs. (ma-eq),
+ *              (sponge_visco)                -- unit conversion, sponge zone
  *   Algorithm 1                               -- order of the steps
  *
  * Where the paper is silent or garbled the reading taken is stated at the
@@ -172,7 +173,25 @@ static void guo_term(double tau, const double *u, const double *F, double *Fi)
  *   f* = f^eq + (1 - 1/tau_eff) f^neq_reg + F_i;
  * keeping a1 makes the momentum gain per step exactly F, as in BGK.
  * collision 1 is plain BGK:  f* = f - (f - f^eq)/tau_eff + F_i. */
-void orc_collide(const orc_domain *d, const double *f, double *out, double *rho_o, double *u_o)
+/* Sponge zone, eq. (sponge_visco): nu_sponge = nu_eff [K xi^p + 1] with
+ * xi = (x - x_start)/(x_end - x_start) inside the zone.
+ * READING: lattice units; the zone is the last sponge_len lattice spacings
+ * before the outlet column, x_end = nx - 1, x_start = x_end - sponge_len;
+ * outside it the factor is 1.  Since nu = c_s^2 (tau - 1/2) (eq. lbe-nu),
+ * the zone's relaxation time is tau = 1/2 + F(x) (tau_eff - 1/2), used for
+ * the whole collision (forcing included).  The factor depends on x only, so
+ * it is defined whatever the x boundary. */
+double orc_sponge_factor(const orc_domain *d, int32_t x)
+{
+    if (!(d->sponge_len > 0.0)) return 1.0;
+    const double xe = (double)(d->nx - 1), xs = xe - d->sponge_len;
+    if ((double)x < xs) return 1.0;
+    const double xi = ((double)x - xs) / (xe - xs);
+    return d->sponge_K * pow(xi, d->sponge_p) + 1.0;
+}
+
+static void collide_nu(const orc_domain *d, const double *f, double *out, double *rho_o, double *u_o,
+                       double nu_factor)
 {
     double rho, u[3], pi[9], feq[Q19], Fi[Q19], fneq[Q19];
     orc_moments(f, d->force, &rho, u, pi);
@@ -180,6 +199,7 @@ void orc_collide(const orc_domain *d, const double *f, double *out, double *rho_
     double q2 = 0.0;
     for (int k = 0; k < 9; ++k) q2 += pi[k] * pi[k];
     double tau = orc_tau_eff(d->tau0, d->c_smag, rho, sqrt(q2));
+    if (nu_factor != 1.0) tau = 0.5 + nu_factor * (tau - 0.5);
     guo_term(tau, u, d->force, Fi);
     if (d->collision == 0) {
         double a1[3] = {0.0, 0.0, 0.0};
@@ -196,6 +216,11 @@ void orc_collide(const orc_domain *d, const double *f, double *out, double *rho_
     }
     if (rho_o) *rho_o = rho;
     if (u_o) for (int a = 0; a < 3; ++a) u_o[a] = u[a];
+}
+
+void orc_collide(const orc_domain *d, const double *f, double *out, double *rho_o, double *u_o)
+{
+    collide_nu(d, f, out, rho_o, u_o, 1.0);
 }
 
 /* Zou-He density at the x = 0 inlet, eqs. (density_bc), (density_bc_sub).
@@ -392,7 +417,7 @@ static void cell_update(const orc_domain *d, int32_t type, const void *src, int 
         for (int a = 0; a < 3; ++a) uo[a] = j[a] / rho;
         orc_outlet_reconstruct(f, uo, f);
     }
-    orc_collide(d, f, out, rho_o, u_o);
+    collide_nu(d, f, out, rho_o, u_o, orc_sponge_factor(d, x));
 }
 
 void orc_cell_update(const orc_domain *d, int32_t src_type, const void *src,

@@ -32,6 +32,8 @@ typedef struct {
     double tau0;         /* molecular relaxation time */
     double c_smag;       /* C of nu_t = C delta^2 |S| */
     double force[3];     /* body-force density (Guo forcing) */
+    double sponge_len;   /* sponge zone length before x = nx-1 (lattice units); 0: off */
+    double sponge_K, sponge_p;  /* eq. (sponge_visco) constants */
 } orc_domain;
 
 typedef struct {
@@ -57,6 +59,7 @@ void   orc_moments(const double *f19, const double *F3, double *rho, double *u3,
 double orc_tau_eff(double tau0, double C, double rho, double Q_half);
 void   orc_regularized_neq(const double *pi_neq9, double *fneq19);
 void   orc_collide(const orc_domain *d, const double *f19, double *out19, double *rho, double *u3);
+double orc_sponge_factor(const orc_domain *d, int32_t x);
 double orc_zou_he_density(const double *f19, double ux);
 void   orc_inlet_reconstruct(const double *f19, const double *u_bc3, double *out19);
 void   orc_outlet_reconstruct(const double *f19, const double *u_out3, double *out19);

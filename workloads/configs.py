@@ -38,6 +38,10 @@ class ChannelCase:
     bc_y: str = "walls"        # "walls" | "periodic"
     force: tuple = (0.0, 0.0, 0.0)
     beta: float = 2.0
+    # sponge zone before the outlet: length in lattice units (0: off), K, p
+    sponge_len: float = 0.0
+    sponge_K: float = 1000.0
+    sponge_p: float = 3.0
 
     @property
     def cells(self) -> int:
