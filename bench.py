@@ -7,6 +7,8 @@ D3Q19 FP32 lattice (h = 64, 200 STG modes), inputs resident in HBM, lattice
 (2.9 GB) far larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload ensemble [--members 64] [--steps K]   (batched ensemble)
+  python bench.py --workload serve [--jobs 60] [--steps-scale 0.1]   (served stream)
 
 N > 1 runs one independent channel per GPU (weak scaling, no collective on
 the data path).  ``--impl reference`` times the CPU FP64 oracle on the host
@@ -312,6 +314,89 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_ensemble(args):
+    """Batched ensemble: 64 independent channels (h from {16, 24, 32, 48, 64},
+    Re_tau from {180, 395}, seeds 1..64) advanced by the batch executor, one
+    CUDA-graph launch per block of steps; the batch's tile comes from the
+    autotuner.  Prints one JSON line (whole-batch MLUPS)."""
+    import torch
+    from paper_2205_02774_gb300 import build
+    build()
+    from paper_2205_02774_gb300.channel import Channel
+    from paper_2205_02774_gb300.serving import Batch
+    from workloads.serving import ensemble
+    jobs = ensemble(args.members, steps=args.steps, storage=args.storage)
+    t0 = time.perf_counter()
+    chans = [Channel.from_case(j.case, check_every=100, mass_tol=0.5) for j in jobs]
+    b = Batch()
+    for ch in chans:
+        b.add(ch)
+    tile = b.autotune(3)
+    t_setup = time.perf_counter() - t0
+    b.step(args.warmup)
+    b.sync()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(args.steps)
+    e1.record(b.stream)
+    e1.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    bad = [i for i, ch in enumerate(chans) if ch.stats()["rc"] != 0]
+    cells = sum(ch.cells for ch in chans)
+    peak, peak_kind = _peaks()
+    bpc = BYTES_PER_CELL[args.storage]
+    value = cells * args.steps / (ms * 1e-3) / 1e6
+    achieved = bpc * cells * args.steps / (ms * 1e-3) / 1e9
+    line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"ensemble of {len(chans)} channels", "storage": args.storage, "cells": cells,
+                       "members": len(chans), "block_steps": b.block_steps, "tile": tile,
+                       "l2": "inputs larger than L2", "setup_s": t_setup},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "scope": "whole step incl. inlet kernels",
+                         "peak_source": f"{peak_kind} hbm_gbs (copy)"},
+            "failed_members": bad, "clocks": clocks}
+    b.close()
+    for ch in chans:
+        ch.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Served stream: Poisson arrivals (2 jobs/s) of channel jobs of 0.5M-20M
+    cells (h = 20..65, aspect 12:2:3), Re_tau from {180, 395}, FP32 or FP16
+    storage, own seeds, step counts uniform in [1000, 20000] x steps_scale,
+    admitted by a 150 GB budget into the continuous-batching loop.  Prints one
+    JSON line (jobs/s, aggregate MLUPS, p50/p99 latency)."""
+    from paper_2205_02774_gb300 import build
+    build()
+    from paper_2205_02774_gb300.serving import serve
+    from workloads.serving import poisson_stream
+    sm = max(1, int(round(1000 * args.steps_scale)))
+    jobs = poisson_stream(args.jobs, rate_per_s=2.0, steps_min=sm, steps_max=max(sm, int(round(20000 * args.steps_scale))))
+    sampler = ClockSampler(0)
+    sampler.start()
+    results, rep = serve(jobs, hbm_budget_bytes=150e9, check_every=100, mass_tol=0.5)
+    clocks = sampler.stop()
+    offered = sum(j.case.cells * j.steps for j in jobs) / max(jobs[-1].arrival_s, 1e-9) / 1e6
+    line = {"metric": "jobs/s", "value": rep["jobs_per_s"], "unit": "jobs/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": f"served stream of {len(jobs)} jobs", "arrival_rate_per_s": 2.0,
+                       "steps_scale": args.steps_scale, "hbm_budget_gb": 150},
+            "aggregate_mlups": rep["aggregate_mlups"], "offered_mlups": offered,
+            "p50_latency_s": rep["p50_latency_s"], "p99_latency_s": rep["p99_latency_s"],
+            "mean_latency_s": rep["mean_latency_s"], "wall_s": rep["wall_s"], "completed": rep["completed"],
+            "failed": rep["failed"], "peak_active": rep["peak_active"],
+            "peak_device_gb": rep["peak_device_bytes"] / 1e9, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,11 +407,18 @@ def main():
     ap.add_argument("--storage", choices=["fp32", "fp16s"], default="fp32")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--members", type=int, default=64, help="ensemble workload: channels in the batch")
+    ap.add_argument("--jobs", type=int, default=60, help="serve workload: jobs in the stream")
+    ap.add_argument("--steps-scale", type=float, default=0.1, help="serve workload: scale of the step counts")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -82,6 +82,13 @@ typedef struct {
     double c_smag;        /* C in nu_t = C delta^2 |S| (C = Cs^2), eq. (smogrinsky_model) */
     double force[3];      /* body-force density, Guo forcing, eq. (bodyforce) */
     double mass_tol;      /* |M/M0 - 1| above this fails the check; <= 0: NaN/Inf only */
+    /* Sponge zone before the outlet, eq. (sponge_visco) (Sec. IV): in the last
+     * sponge_len lattice spacings before x_end = nx - 1 (x_start = x_end -
+     * sponge_len) the viscosity is nu_eff [K xi^p + 1], xi = (x - x_start) /
+     * sponge_len, i.e. tau = 1/2 + [K xi^p + 1] (tau_eff - 1/2).  sponge_len = 0
+     * switches it off (the paper: 0.4 half-heights, K = 1000, p = 3).  The
+     * factor depends on x only; a sponge needs force = 0. */
+    double sponge_len, sponge_K, sponge_p;
 } stg_domain;
 
 /* RANS interface profile on wall-normal finite-volume cells (Algorithm 1,
@@ -180,6 +187,12 @@ int stg_lbm_stats(stg_lbm *h, stg_stats *out);
 int stg_lbm_get_state(stg_lbm *h, void *host, size_t bytes);
 int stg_lbm_set_state(stg_lbm *h, const void *host, size_t bytes, int64_t step);
 
+/* Copy a sub-block of the current populations (storage format) to host
+ * memory: cells x0..x0+bx-1, y0.., z0.., layout [19][bz][by][bx].  The block
+ * must lie inside the lattice.  Errors: STG_ERR_INVALID, STG_ERR_CUDA. */
+int stg_lbm_get_block(stg_lbm *h, int32_t x0, int32_t y0, int32_t z0, int32_t bx, int32_t by, int32_t bz,
+                      void *host);
+
 /* Copy the inlet velocity of the last completed step (3*nz*ny floats, lattice
  * units, layout u[c][z][y]) to host memory. */
 int stg_lbm_get_inlet(stg_lbm *h, float *host_u);
@@ -214,6 +227,17 @@ typedef struct {
 int stg_lbm_set_tile(stg_lbm *h, const stg_tile *tile);
 int stg_lbm_get_tile(const stg_lbm *h, stg_tile *tile);
 
+/* Velocity probes for time series (the auto-correlation B_uu and the
+ * integral time scale of Sec. V, eq. (time-integral)).  set_probes stores n
+ * cells (xyz: 3 n host int32, x y z each inside the lattice; n = 0 clears).
+ * step_probed advances n >= 1 steps like stg_lbm_step and after every step
+ * samples the velocity u = (sum_i c_i f_i - F/2)/rho of each probe cell from
+ * the stored populations; u_host receives n x n_probes x 3 floats (step-major)
+ * and the call returns after the copy.  Errors: STG_ERR_INVALID (no probes,
+ * bad sizes), STG_ERR_NOMEM, and those of stg_lbm_step. */
+int stg_lbm_set_probes(stg_lbm *h, int32_t n, const int32_t *xyz);
+int stg_lbm_step_probed(stg_lbm *h, int64_t n, float *u_host);
+
 /* Autotuner: time every candidate tile on this lattice (`trial_passes` >= 1
  * plain step passes each, CUDA events on the handle's stream, after one
  * warm-up pass), keep the fastest and store it in *chosen (may be NULL).
@@ -231,6 +255,117 @@ const char *stg_lbm_last_error(const stg_lbm *h);
 /* The 4*n uniform draws in [0,1) used for n modes (per mode: Phi, gamma, eta,
  * phi), SplitMix64 of `seed` (Steele, Lea & Flood 2014), top 53 bits. */
 int stg_mode_draws(uint64_t seed, int32_t n, double *out);
+
+/* Device bytes that stg_lbm_create would take for this domain (an upper
+ * bound: with n_modes = 0 the mode count is bounded by its largest value for
+ * this ny).  `stg` may be NULL for periodic-x domains.  Used for admission by
+ * memory budget.  Errors: STG_ERR_INVALID. */
+int stg_lbm_estimate_bytes(const stg_domain *domain, const stg_params *stg, int64_t *bytes);
+
+/* ---------------------------------------------------------------------------
+ * Batch executor.  The paper runs one channel; the batch runs an ensemble of
+ * independent lattices together.  Each block of B steps is one CUDA-graph
+ * launch in which every member's chain of B steps (inlet kernel, then the
+ * step pass with its boundary branch) is its own branch, so small lattices
+ * fill the GPU together and no member waits for another between steps.  B is
+ * the smallest multiple of 2 and of every member's sampling period that is at
+ * least 16 (members whose periods have no common multiple <= 256 are
+ * refused).  A member runs exactly the kernels and arguments it runs alone:
+ * its populations and statistics are bit-identical to a solo run.  Members
+ * keep their own state, statistics and mass checks; stg_lbm_stats,
+ * get_state, get_inlet, device_state and info work on a member as usual and
+ * are ordered after the batch's work; stg_lbm_step, step_timed, set_state,
+ * set_tile and autotune return STG_ERR_INVALID while it is a member.
+ * Destroying a member takes it out of its batch first. */
+typedef struct stg_batch stg_batch;
+
+/* Empty batch ordered on `stream` (NULL: the batch creates a non-blocking
+ * stream of its own).  Errors: STG_ERR_INVALID, STG_ERR_CUDA. */
+int stg_batch_create(void *stream, stg_batch **out);
+/* Add / remove a member (same device).  remove() leaves the lattice usable on
+ * its own.  Errors: STG_ERR_INVALID, STG_ERR_CUDA. */
+int stg_batch_add(stg_batch *b, stg_lbm *h);
+int stg_batch_remove(stg_batch *b, stg_lbm *h);
+int stg_batch_size(const stg_batch *b);
+/* Steps per block graph (B above). */
+int stg_batch_block_steps(const stg_batch *b);
+/* Advance every member by n >= 0 steps (asynchronous): whole blocks replay
+ * the block graph, the rest runs as each member's single-step graphs.
+ * Returns the first member error a completed check reported
+ * (STG_ERR_UNSTABLE; the message names the member's index), else STG_OK or
+ * STG_ERR_CUDA. */
+int stg_batch_step(stg_batch *b, int64_t n);
+/* Wait for the batch's work (bounded; STG_ERR_TIMEOUT). */
+int stg_batch_sync(stg_batch *b);
+/* Autotuner for the batch: every candidate tile is timed over `trial_passes`
+ * concurrent plain passes of all members (no state advance, as in
+ * stg_lbm_autotune); the fastest is set on every member. */
+int stg_batch_autotune(stg_batch *b, int32_t trial_passes, stg_tile *chosen);
+/* Release the members (they stay alive) and the batch (NULL-safe). */
+void stg_batch_destroy(stg_batch *b);
+/* Message of the last error on b (b may be NULL: last create() error). */
+const char *stg_batch_last_error(const stg_batch *b);
+
+/* ---------------------------------------------------------------------------
+ * Serving loop (no counterpart in the paper): a stream of channel jobs with
+ * arrival times is run with continuous batching.  In arrival order, a job is
+ * admitted once it has arrived, a slot is free (max_active) and its device
+ * memory (stg_lbm_estimate_bytes) fits the budget next to the running jobs; it
+ * joins the running batch at the next block boundary, so its work overlaps
+ * with the jobs already on the GPU.  A job whose remaining steps are fewer
+ * than one block leaves the batch and finishes on its own stream; its FP64
+ * statistics are copied to the caller's buffers, its memory is freed and the
+ * next job can be admitted.  Jobs are independent: each result equals that
+ * of the same job run alone.  A job larger than the budget fails with
+ * STG_ERR_NOMEM; a job that fails its checks gets that status and the others
+ * continue. */
+typedef struct {
+    double arrival_s;              /* seconds after the start of the run */
+    const stg_domain *domain;      /* as for stg_lbm_create */
+    const stg_rans_profile *rans;
+    const stg_params *stg;
+    uint64_t seed;
+    int64_t steps;                 /* >= 1 */
+    double *mean_sum;              /* optional outputs, caller-owned: 3*nx*ny and */
+    double *rey_sum;               /* 6*nx*ny doubles as in stg_stats (NULL: skipped) */
+} stg_job;
+
+typedef struct {
+    int32_t status;                /* STG_OK or the job's error */
+    int32_t pad0;
+    double admit_s, finish_s;      /* seconds after the start of the run */
+    double latency_s;              /* finish_s - arrival_s */
+    int64_t n_samples;             /* statistics samples accumulated */
+    int64_t device_bytes;          /* admission estimate */
+    double mass, mass0;            /* FP64 mass at the end / after create */
+} stg_job_result;
+
+typedef struct {
+    double hbm_budget_bytes;       /* device memory the admitted jobs may hold together */
+    int32_t max_active;            /* jobs running at once (<= 0: no limit) */
+    int32_t pad0;
+} stg_serve_config;
+
+typedef struct {
+    double wall_s;                 /* start of the run to the last completion */
+    double jobs_per_s;             /* completed jobs / wall_s */
+    double aggregate_mlups;        /* cell updates of the completed jobs / wall_s / 1e6 */
+    double p50_latency_s, p99_latency_s, mean_latency_s;
+    int64_t completed, failed;
+    int64_t cell_updates;
+    int64_t peak_device_bytes;     /* largest admitted estimate total */
+    int32_t peak_active;
+    int32_t pad0;
+} stg_serve_report;
+
+/* Run the jobs (arrival times relative to the call) and return when all
+ * have completed or failed.  `stream` orders the batch's work (NULL: own).
+ * results[i] belongs to jobs[i].  Errors: STG_ERR_INVALID (arguments),
+ * STG_ERR_CUDA / STG_ERR_TIMEOUT (the run itself). */
+int stg_serve_run(const stg_job *jobs, int32_t n_jobs, const stg_serve_config *cfg, void *stream,
+                  stg_job_result *results, stg_serve_report *report);
+/* Message of the last stg_serve_run error on this thread. */
+const char *stg_serve_last_error(void);
 
 /* Library version string. */
 const char *stg_lbm_version(void);

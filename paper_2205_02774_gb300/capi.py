@@ -28,7 +28,8 @@ class stg_domain(C.Structure):
                 ("collision", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32),
                 ("stats_every", C.c_int32), ("check_every", C.c_int32), ("pad0", C.c_int32),
                 ("tau0", C.c_double), ("c_smag", C.c_double), ("force", C.c_double * 3),
-                ("mass_tol", C.c_double)]
+                ("mass_tol", C.c_double), ("sponge_len", C.c_double), ("sponge_K", C.c_double),
+                ("sponge_p", C.c_double)]
 
 
 class stg_rans_profile(C.Structure):
@@ -66,6 +67,29 @@ class stg_info(C.Structure):
                 ("n_modes", C.c_int64), ("device_bytes", C.c_int64)]
 
 
+class stg_job(C.Structure):
+    _fields_ = [("arrival_s", C.c_double), ("domain", C.POINTER(stg_domain)), ("rans", C.POINTER(stg_rans_profile)),
+                ("stg", C.POINTER(stg_params)), ("seed", C.c_uint64), ("steps", C.c_int64),
+                ("mean_sum", c_double_p), ("rey_sum", c_double_p)]
+
+
+class stg_job_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("pad0", C.c_int32), ("admit_s", C.c_double), ("finish_s", C.c_double),
+                ("latency_s", C.c_double), ("n_samples", C.c_int64), ("device_bytes", C.c_int64),
+                ("mass", C.c_double), ("mass0", C.c_double)]
+
+
+class stg_serve_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_double), ("max_active", C.c_int32), ("pad0", C.c_int32)]
+
+
+class stg_serve_report(C.Structure):
+    _fields_ = [("wall_s", C.c_double), ("jobs_per_s", C.c_double), ("aggregate_mlups", C.c_double),
+                ("p50_latency_s", C.c_double), ("p99_latency_s", C.c_double), ("mean_latency_s", C.c_double),
+                ("completed", C.c_int64), ("failed", C.c_int64), ("cell_updates", C.c_int64),
+                ("peak_device_bytes", C.c_int64), ("peak_active", C.c_int32), ("pad0", C.c_int32)]
+
+
 _SIGNATURES = {
     "stg_lbm_create": (C.c_int, [C.POINTER(stg_domain), C.POINTER(stg_rans_profile), C.POINTER(stg_params),
                                  C.c_uint64, C.POINTER(stg_allocator), C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -80,6 +104,24 @@ _SIGNATURES = {
     "stg_lbm_set_tile": (C.c_int, [C.c_void_p, C.POINTER(stg_tile)]),
     "stg_lbm_get_tile": (C.c_int, [C.c_void_p, C.POINTER(stg_tile)]),
     "stg_lbm_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(stg_tile)]),
+    "stg_lbm_get_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                    C.c_void_p]),
+    "stg_lbm_set_probes": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "stg_lbm_step_probed": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_float)]),
+    "stg_lbm_estimate_bytes": (C.c_int, [C.POINTER(stg_domain), C.POINTER(stg_params), C.POINTER(C.c_int64)]),
+    "stg_batch_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "stg_batch_add": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "stg_batch_remove": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "stg_batch_size": (C.c_int, [C.c_void_p]),
+    "stg_batch_block_steps": (C.c_int, [C.c_void_p]),
+    "stg_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "stg_batch_sync": (C.c_int, [C.c_void_p]),
+    "stg_batch_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(stg_tile)]),
+    "stg_batch_destroy": (None, [C.c_void_p]),
+    "stg_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "stg_serve_run": (C.c_int, [C.POINTER(stg_job), C.c_int32, C.POINTER(stg_serve_config), C.c_void_p,
+                                C.POINTER(stg_job_result), C.POINTER(stg_serve_report)]),
+    "stg_serve_last_error": (C.c_char_p, []),
     "stg_lbm_destroy": (None, [C.c_void_p]),
     "stg_lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "stg_mode_draws": (C.c_int, [C.c_uint64, C.c_int32, c_double_p]),
@@ -215,3 +257,87 @@ def stg_lattice_mass_noalloc(pops_dev, storage, nx, ny, nz, mass_out_dev, stream
     (a device double) without any allocation; returns the status code."""
     return lib().stg_lattice_mass_noalloc(C.c_void_p(pops_dev), storage, nx, ny, nz, C.c_void_p(mass_out_dev),
                                           C.c_void_p(stream))
+
+
+# ---------------------------------------------------------------- estimate, batch, serving
+def stg_lbm_estimate_bytes(domain, params=None):
+    out = C.c_int64()
+    _check(lib().stg_lbm_estimate_bytes(C.byref(domain), C.byref(params) if params is not None else None,
+                                        C.byref(out)))
+    return out.value
+
+
+def _bcheck(rc, b):
+    if rc != STG_OK:
+        msg = lib().stg_batch_last_error(b)
+        raise StgError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def stg_batch_create(stream=0):
+    b = C.c_void_p()
+    _bcheck(lib().stg_batch_create(C.c_void_p(stream), C.byref(b)), None)
+    return b
+
+
+def stg_batch_add(b, h):
+    return _bcheck(lib().stg_batch_add(b, h), b)
+
+
+def stg_batch_remove(b, h):
+    return _bcheck(lib().stg_batch_remove(b, h), b)
+
+
+def stg_batch_size(b):
+    return lib().stg_batch_size(b)
+
+
+def stg_batch_block_steps(b):
+    return lib().stg_batch_block_steps(b)
+
+
+def stg_batch_step(b, n):
+    return _bcheck(lib().stg_batch_step(b, n), b)
+
+
+def stg_batch_sync(b):
+    return _bcheck(lib().stg_batch_sync(b), b)
+
+
+def stg_batch_autotune(b, trial_passes=10):
+    t = stg_tile()
+    _bcheck(lib().stg_batch_autotune(b, trial_passes, C.byref(t)), b)
+    return t.interior_layout, t.interior_zc, t.wall_zc
+
+
+def stg_batch_destroy(b):
+    lib().stg_batch_destroy(b)
+
+
+def stg_serve_run(jobs, cfg, stream=0):
+    """jobs: a ctypes array of stg_job; returns (rc, results array, report)."""
+    n = len(jobs)
+    res = (stg_job_result * max(n, 1))()
+    rep = stg_serve_report()
+    rc = lib().stg_serve_run(jobs, n, C.byref(cfg), C.c_void_p(stream), res, C.byref(rep))
+    if rc != STG_OK:
+        msg = lib().stg_serve_last_error()
+        raise StgError(rc, msg.decode() if msg else "")
+    return res, rep
+
+
+def stg_lbm_set_probes(h, xyz):
+    a = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    return _check(lib().stg_lbm_set_probes(h, a.shape[0], a.ctypes.data_as(C.POINTER(C.c_int32))), h)
+
+
+def stg_lbm_step_probed(h, n, n_probes):
+    out = np.empty((n, n_probes, 3), dtype=np.float32)
+    _check(lib().stg_lbm_step_probed(h, n, out.ctypes.data_as(C.POINTER(C.c_float))), h)
+    return out
+
+
+def stg_lbm_get_block(h, x0, y0, z0, out):
+    """out: host array [19][bz][by][bx] of the storage dtype."""
+    _, bz, by, bx = out.shape
+    return _check(lib().stg_lbm_get_block(h, x0, y0, z0, bx, by, bz, C.c_void_p(out.ctypes.data)), h)

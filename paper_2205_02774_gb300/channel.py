@@ -38,8 +38,9 @@ class _TorchAllocator:
 
 
 def _domain(nx, ny, nz, storage, collision, bc_x, bc_y, stats_every, check_every, tau0, c_smag, force,
-            mass_tol):
+            mass_tol, sponge=(0.0, 1000.0, 3.0)):
     d = A.stg_domain()
+    d.sponge_len, d.sponge_K, d.sponge_p = sponge
     d.nx, d.ny, d.nz = nx, ny, nz
     d.storage = {"fp32": A.STG_FP32, "fp16s": A.STG_FP16_SHIFTED}[storage]
     d.collision = {"regularized": A.STG_REGULARIZED, "bgk": A.STG_BGK}[collision]
@@ -52,6 +53,39 @@ def _domain(nx, ny, nz, storage, collision, bc_x, bc_y, stats_every, check_every
     return d
 
 
+def create_structs(nx, ny, nz, *, profile=None, tau0=0.52, c_smag=0.01, force=(0.0, 0.0, 0.0), storage="fp32",
+                   collision="regularized", bc_x="stg", bc_y="walls", stats_every=0, check_every=0, mass_tol=0.0,
+                   n_modes=100, C_l=3.0, alpha=0.01, t_filter=0.0, mach_target=0.0516, sponge=(0.0, 1000.0, 3.0)):
+    """The stg_domain, stg_rans_profile and stg_params of a lattice (the last
+    two None for periodic x), plus the arrays they point into (keep them
+    alive while the structs are in use).  sponge = (length, K, p)."""
+    domain = _domain(nx, ny, nz, storage, collision, bc_x, bc_y, stats_every, check_every, tau0, c_smag, force,
+                     mass_tol, sponge)
+    keep = []
+    rans = None
+    params = None
+    if bc_x == "stg":
+        arrays = [np.ascontiguousarray(getattr(profile, k), dtype=np.float64) for k in ("y_c", "U", "k", "eps")]
+        arrays.append(np.ascontiguousarray(profile.R, dtype=np.float64).reshape(-1))
+        keep += arrays
+        rans = A.stg_rans_profile()
+        rans.n_fv = arrays[0].size
+        rans.y_c, rans.U, rans.k, rans.eps, rans.R = [a.ctypes.data_as(A.c_double_p) for a in arrays]
+        rans.U_bulk, rans.nu_phys, rans.h_phys = profile.U_bulk, profile.nu_phys, profile.h_phys
+        rans.mach_target = mach_target
+        params = A.stg_params()
+        params.n_modes, params.C_l, params.alpha, params.T_filter = n_modes, C_l, alpha, t_filter
+    return domain, rans, params, keep
+
+
+def case_kwargs(case):
+    """create_structs / Channel keyword arguments of a workload case."""
+    return dict(profile=case.profile() if case.bc_x == "stg" else None, tau0=case.tau0, c_smag=case.c_smag,
+                force=case.force, storage=case.storage, collision=case.collision, bc_x=case.bc_x, bc_y=case.bc_y,
+                stats_every=case.stats_every, n_modes=case.n_modes, t_filter=case.t_filter,
+                mach_target=case.mach_target, sponge=(case.sponge_len, case.sponge_K, case.sponge_p))
+
+
 class Channel:
     """One STG-LBM lattice on the current CUDA device.
 
@@ -61,40 +95,26 @@ class Channel:
     def __init__(self, nx, ny, nz, *, profile=None, tau0=0.52, c_smag=0.01, force=(0.0, 0.0, 0.0),
                  storage="fp32", collision="regularized", bc_x="stg", bc_y="walls", stats_every=0,
                  check_every=0, mass_tol=0.0, n_modes=100, C_l=3.0, alpha=0.01, t_filter=0.0,
-                 mach_target=0.0516, seed=0, stream=None, use_torch_allocator=True):
+                 mach_target=0.0516, seed=0, stream=None, use_torch_allocator=True, sponge=(0.0, 1000.0, 3.0)):
         import torch
         self.torch = torch
         self.nx, self.ny, self.nz = nx, ny, nz
         self.storage = storage
         self.device = torch.cuda.current_device()
         self.stream = stream if stream is not None else torch.cuda.Stream()
-        self.domain = _domain(nx, ny, nz, storage, collision, bc_x, bc_y, stats_every, check_every, tau0,
-                              c_smag, force, mass_tol)
-        self._keep = []
-        rans = None
-        params = None
-        if bc_x == "stg":
-            arrays = [np.ascontiguousarray(getattr(profile, k), dtype=np.float64) for k in
-                      ("y_c", "U", "k", "eps")]
-            arrays.append(np.ascontiguousarray(profile.R, dtype=np.float64).reshape(-1))
-            self._keep += arrays
-            rans = A.stg_rans_profile()
-            rans.n_fv = arrays[0].size
-            rans.y_c, rans.U, rans.k, rans.eps, rans.R = [a.ctypes.data_as(A.c_double_p) for a in arrays]
-            rans.U_bulk, rans.nu_phys, rans.h_phys = profile.U_bulk, profile.nu_phys, profile.h_phys
-            rans.mach_target = mach_target
-            params = A.stg_params()
-            params.n_modes, params.C_l, params.alpha, params.T_filter = n_modes, C_l, alpha, t_filter
+        self.domain, rans, params, self._keep = create_structs(
+            nx, ny, nz, profile=profile, tau0=tau0, c_smag=c_smag, force=force, storage=storage,
+            collision=collision, bc_x=bc_x, bc_y=bc_y, stats_every=stats_every, check_every=check_every,
+            mass_tol=mass_tol, n_modes=n_modes, C_l=C_l, alpha=alpha, t_filter=t_filter, mach_target=mach_target,
+            sponge=sponge)
         self._allocator = _TorchAllocator(torch, self.device, self.stream) if use_torch_allocator else None
         self.h = A.stg_lbm_create(self.domain, rans, params, seed,
                                   self._allocator.struct if self._allocator else None, self.stream.cuda_stream)
 
     @classmethod
     def from_case(cls, case, **kw):
-        args = dict(profile=case.profile() if case.bc_x == "stg" else None, tau0=case.tau0, c_smag=case.c_smag,
-                    force=case.force, storage=case.storage, collision=case.collision, bc_x=case.bc_x,
-                    bc_y=case.bc_y, stats_every=case.stats_every, n_modes=case.n_modes, t_filter=case.t_filter,
-                    mach_target=case.mach_target, seed=case.seed)
+        args = case_kwargs(case)
+        args["seed"] = case.seed
         args.update(kw)
         return cls(case.nx, case.ny, case.nz, **args)
 
@@ -123,12 +143,26 @@ class Channel:
     def autotune(self, trial_passes=10):
         return A.stg_lbm_autotune(self.h, trial_passes)
 
+    def set_probes(self, xyz):
+        self._n_probes = int(np.asarray(xyz).reshape(-1, 3).shape[0])
+        A.stg_lbm_set_probes(self.h, xyz)
+
+    def step_probed(self, n):
+        """n steps; returns the probe velocities after each, shape (n, n_probes, 3)."""
+        return A.stg_lbm_step_probed(self.h, n, self._n_probes)
+
     def step_timed(self, n):
         return A.stg_lbm_step_timed(self.h, n)
 
     def get_state(self):
         out = np.empty(self.shape, dtype=self.state_dtype)
         A.stg_lbm_get_state(self.h, out)
+        return out
+
+    def get_block(self, x0, y0, z0, bx, by, bz):
+        """Sub-block [19][bz][by][bx] of the current populations (storage format)."""
+        out = np.empty((19, bz, by, bx), dtype=self.state_dtype)
+        A.stg_lbm_get_block(self.h, x0, y0, z0, out)
         return out
 
     def set_state(self, arr, step=0):

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstglbm.so")
-SOURCES = ["capi.cu", "step_kernel.cu", "inlet_kernel.cu", "tma_kernel.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "step_kernel.cu", "inlet_kernel.cu", "tma_kernel.cu", "noalloc.cu", "batch.cu", "serve.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE,
               "--expt-relaxed-constexpr"]

@@ -279,6 +279,7 @@ stg::StepArgs step_args(const stg_lbm *h, int parity)
     a.Fz = (float)h->d.force[2];
     a.has_force = (h->d.force[0] != 0.0 || h->d.force[1] != 0.0 || h->d.force[2] != 0.0);
     a.ubc = h->ubc;
+    a.spf = h->spf;
     a.ctl = h->ctl;
     a.parity = parity;
     a.stats_every = h->d.stats_every;
@@ -525,6 +526,7 @@ int reset_counters(stg_lbm *h, int64_t step)
 void release(stg_lbm *h)
 {
     if (!h) return;
+    if (h->batch) batch_detach(h);
     if (h->stream) cudaStreamSynchronize(h->stream);
     destroy_graphs(h);
     for (auto &a : h->allocs) {
@@ -558,6 +560,14 @@ int validate(const stg_domain *d, const stg_rans_profile *r, const stg_params *p
     if (d->stats_every < 0 || d->check_every < 0) return fail(nullptr, STG_ERR_INVALID, "negative cadence");
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(d->force[a])) return fail(nullptr, STG_ERR_INVALID, "non-finite force");
+    if (!(d->sponge_len >= 0.0) || !std::isfinite(d->sponge_len))
+        return fail(nullptr, STG_ERR_INVALID, "sponge_len must be finite and >= 0");
+    if (d->sponge_len > 0.0) {
+        if (!(d->sponge_K >= 0.0) || !std::isfinite(d->sponge_K) || !(d->sponge_p >= 0.0) || !std::isfinite(d->sponge_p))
+            return fail(nullptr, STG_ERR_INVALID, "sponge K and p must be finite and >= 0");
+        if (d->force[0] != 0.0 || d->force[1] != 0.0 || d->force[2] != 0.0)
+            return fail(nullptr, STG_ERR_INVALID, "a sponge zone needs force = 0");
+    }
     if (d->bc_x == STG_BC_X_INLET_OUTLET) {
         if (d->nx < 3) return fail(nullptr, STG_ERR_INVALID, "inlet/outlet needs nx >= 3");
         if (!r || !p) return fail(nullptr, STG_ERR_INVALID, "inlet/outlet needs a RANS profile and STG parameters");
@@ -648,6 +658,20 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
     h->m_partial = (double *)dalloc(h, sizeof(double) * stg::mass_grid_blocks());
     h->m_counter = (unsigned *)dalloc(h, sizeof(unsigned) * 4);
     h->m_out = (double *)dalloc(h, sizeof(double) * 2);
+    if (domain->sponge_len > 0.0) {
+        // eq. (sponge_visco): factor per column, FP64 on the host
+        std::vector<float> f(nx);
+        const double xe = nx - 1.0, xs = xe - domain->sponge_len;
+        for (int x = 0; x < nx; ++x) {
+            const double xi = (x - xs) / (xe - xs);
+            f[x] = x < xs ? 1.0f : (float)(domain->sponge_K * std::pow(xi, domain->sponge_p) + 1.0);
+        }
+        h->spf = (float *)dalloc(h, sizeof(float) * nx);
+        if (!h->spf || cudaMemcpy(h->spf, f.data(), sizeof(float) * nx, cudaMemcpyHostToDevice) != cudaSuccess) {
+            h->err = "sponge table";
+            return bail(STG_ERR_NOMEM);
+        }
+    }
     if (!h->lat[0] || !h->lat[1] || !h->ubc || !h->uf || !h->ctl || !h->stat_mean || !h->stat_rey ||
         !h->mass_partial || !h->mass_counter || !h->mass_out || !h->m_partial || !h->m_counter || !h->m_out) {
         h->err = "device allocation failed";
@@ -696,9 +720,32 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
     return STG_OK;
 }
 
+int stg_lbm_estimate_bytes(const stg_domain *d, const stg_params *p, int64_t *bytes)
+{
+    if (!d || !bytes || d->nx < 1 || d->ny < 1 || d->nz < 1 || (d->storage != STG_FP32 && d->storage != STG_FP16_SHIFTED))
+        return fail(nullptr, STG_ERR_INVALID, "estimate: bad domain");
+    auto r = [](double b) { return (double)(((int64_t)std::max(b, 16.0) + 255) & ~int64_t(255)); };
+    const double nx = d->nx, ny = d->ny, nz = d->nz, P = nx * ny * nz;
+    const double elem = d->storage == STG_FP32 ? 4.0 : 2.0;
+    double b = 2 * r(19 * P * elem) + 2 * r(12 * ny * nz) + r(sizeof(StepCtl)) + r(24 * nx * ny) + r(48 * nx * ny) +
+               r(8.0 * stg::step_grid_blocks(d->nx, d->ny, d->nz)) + 2 * r(16) + 2 * r(16) +
+               r(8.0 * stg::mass_grid_blocks());
+    if (d->bc_x == STG_BC_X_INLET_OUTLET) {
+        double N = 1.0;
+        if (p && p->n_modes > 0) N = p->n_modes;
+        else if (p && p->alpha > 0.0) N = std::ceil(std::log(1.5 * std::max(ny, 2.0)) / std::log(1.0 + p->alpha) + 1.0);
+        if (d->sponge_len > 0.0) b += r(4 * nx);
+        b += r(4 * N * ny) + r(4 * N * nz) + r(4 * N * ny) + r(12 * N) + 2 * r(8 * N) + r(24 * ny) + r(4 * ny) +
+             r(48 * ny) + r(24 * ny) + r(16 * N);
+    }
+    *bytes = (int64_t)b;
+    return STG_OK;
+}
+
 int stg_lbm_step(stg_lbm *h, int64_t n)
 {
     if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
+    if (h->batch) return fail(h, STG_ERR_INVALID, "the lattice is in a batch; step the batch");
     if (n < 0) return fail(h, STG_ERR_INVALID, "negative step count");
     int rc = poll_check(h);
     if (rc) return rc;
@@ -725,6 +772,7 @@ int stg_lbm_step(stg_lbm *h, int64_t n)
 int stg_lbm_step_timed(stg_lbm *h, int64_t n, double *ms_step, double *ms_inlet)
 {
     if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
+    if (h->batch) return fail(h, STG_ERR_INVALID, "the lattice is in a batch; step the batch");
     if (n < 1 || n > 4096) return fail(h, STG_ERR_INVALID, "step_timed needs 1 <= n <= 4096");
     if (h->sticky) return fail(h, h->sticky, "an earlier check failed; reset the state first");
     std::vector<cudaEvent_t> ev(3 * (size_t)n, nullptr);
@@ -807,6 +855,7 @@ int stg_lbm_get_state(stg_lbm *h, void *host, size_t bytes)
 int stg_lbm_set_state(stg_lbm *h, const void *host, size_t bytes, int64_t step)
 {
     if (!h || !host) return fail(h, STG_ERR_INVALID, "NULL argument");
+    if (h->batch) return fail(h, STG_ERR_INVALID, "the lattice is in a batch; remove it first");
     if (bytes != 19 * h->P * h->elem) return fail(h, STG_ERR_INVALID, "state size mismatch");
     if (step < 0) return fail(h, STG_ERR_INVALID, "negative step");
     int rc = wait_stream(h);
@@ -815,6 +864,29 @@ int stg_lbm_set_state(stg_lbm *h, const void *host, size_t bytes, int64_t step)
     rc = reset_counters(h, step);
     if (rc) return rc;
     return compute_mass(h, &h->mass0);
+}
+
+int stg_lbm_get_block(stg_lbm *h, int32_t x0, int32_t y0, int32_t z0, int32_t bx, int32_t by, int32_t bz, void *host)
+{
+    if (!h || !host) return fail(h, STG_ERR_INVALID, "NULL argument");
+    if (bx < 1 || by < 1 || bz < 1 || x0 < 0 || y0 < 0 || z0 < 0 || x0 + bx > h->d.nx || y0 + by > h->d.ny ||
+        z0 + bz > h->d.nz)
+        return fail(h, STG_ERR_INVALID, "block outside the lattice");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    // one 3-D copy per population: rows of bx elements
+    for (int i = 0; i < 19; ++i) {
+        cudaMemcpy3DParms m{};
+        char *base = static_cast<char *>(h->lat[h->t & 1]) + (size_t)i * h->P * h->elem;
+        m.srcPtr = make_cudaPitchedPtr(base, (size_t)h->d.nx * h->elem, (size_t)h->d.nx, (size_t)h->d.ny);
+        m.srcPos = make_cudaPos((size_t)x0 * h->elem, (size_t)y0, (size_t)z0);
+        char *dst = static_cast<char *>(host) + (size_t)i * bx * by * bz * h->elem;
+        m.dstPtr = make_cudaPitchedPtr(dst, (size_t)bx * h->elem, (size_t)bx, (size_t)by);
+        m.extent = make_cudaExtent((size_t)bx * h->elem, (size_t)by, (size_t)bz);
+        m.kind = cudaMemcpyDeviceToHost;
+        CK(cudaMemcpy3DAsync(&m, h->stream));
+    }
+    return wait_stream(h);
 }
 
 int stg_lbm_get_inlet(stg_lbm *h, float *host_u)
@@ -844,18 +916,60 @@ int stg_lbm_info(const stg_lbm *h, stg_info *out)
 int stg_lbm_set_tile(stg_lbm *h, const stg_tile *tile)
 {
     if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
-    if (!tile || !tile_ok(*tile)) return fail(h, STG_ERR_INVALID, "tile: layout 0 or 1, z chunks 0 or >= 4");
+    if (h->batch) return fail(h, STG_ERR_INVALID, "the lattice is in a batch; set the batch's tile");
+    if (!tile) return fail(h, STG_ERR_INVALID, "tile is NULL");
+    return apply_tile(h, *tile);
+}
+
+int stg_lbm_set_probes(stg_lbm *h, int32_t n, const int32_t *xyz)
+{
+    if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
+    if (n < 0 || n > (1 << 20) || (n > 0 && !xyz)) return fail(h, STG_ERR_INVALID, "probes: 0 <= n <= 2^20");
+    for (int32_t k = 0; k < n; ++k)
+        if (xyz[3 * k] < 0 || xyz[3 * k] >= h->d.nx || xyz[3 * k + 1] < 0 || xyz[3 * k + 1] >= h->d.ny ||
+            xyz[3 * k + 2] < 0 || xyz[3 * k + 2] >= h->d.nz)
+            return fail(h, STG_ERR_INVALID, "probe outside the lattice");
     int rc = wait_stream(h);
     if (rc) return rc;
-    const stg_tile old = h->tile;
-    h->tile = *tile;
-    h->tile.pad0 = 0;
-    rc = capture_all(h);
-    if (rc) {
-        h->tile = old;
-        capture_all(h);
+    if (n > h->n_probes || !h->probe_xyz) {
+        h->probe_xyz = (int *)dalloc(h, sizeof(int) * 3 * (size_t)std::max(n, 1));
+        if (!h->probe_xyz) return fail(h, STG_ERR_NOMEM, "probe table");
     }
-    return rc;
+    if (n > 0) CK(cudaMemcpy(h->probe_xyz, xyz, sizeof(int) * 3 * (size_t)n, cudaMemcpyHostToDevice));
+    h->n_probes = n;
+    return STG_OK;
+}
+
+int stg_lbm_step_probed(stg_lbm *h, int64_t n, float *u_host)
+{
+    if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
+    if (h->batch) return fail(h, STG_ERR_INVALID, "the lattice is in a batch; step the batch");
+    if (n < 1 || n > 65536 || !u_host) return fail(h, STG_ERR_INVALID, "step_probed needs 1 <= n <= 65536 and a buffer");
+    if (h->n_probes < 1) return fail(h, STG_ERR_INVALID, "no probes set");
+    int rc = poll_check(h);
+    if (rc) return rc;
+    if (h->sticky) return fail(h, h->sticky, "an earlier check failed; reset the state first");
+    const size_t need = (size_t)n * h->n_probes * 3;
+    if (need > h->probe_cap) {
+        h->probe_buf = (float *)dalloc(h, sizeof(float) * need);
+        if (!h->probe_buf) {
+            h->probe_cap = 0;
+            return fail(h, STG_ERR_NOMEM, "probe buffer");
+        }
+        h->probe_cap = need;
+    }
+    const int64_t t_before = h->t;
+    for (int64_t s = 0; s < n; ++s) {
+        CK(cudaGraphLaunch(h->g_single[h->t & 1][is_stats_step(h, h->t) ? 1 : 0], h->stream));
+        h->t += 1;
+        CK(stg::launch_probe(h->lat[h->t & 1], h->d.storage, h->P, h->d.nx, h->d.ny, h->n_probes, h->probe_xyz,
+                             (float)h->d.force[0], (float)h->d.force[1], (float)h->d.force[2],
+                             h->probe_buf + (size_t)s * h->n_probes * 3, h->stream));
+    }
+    rc = queue_check_readback(h, t_before);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(u_host, h->probe_buf, sizeof(float) * need, cudaMemcpyDeviceToHost, h->stream));
+    return wait_stream(h);
 }
 
 int stg_lbm_get_tile(const stg_lbm *h, stg_tile *tile)
@@ -865,13 +979,60 @@ int stg_lbm_get_tile(const stg_lbm *h, stg_tile *tile)
     return STG_OK;
 }
 
+}  // extern "C"
+
+namespace stg {
+namespace host {
+
+cudaError_t trial_pass(stg_lbm *h, const stg_tile &tile, cudaStream_t s)
+{
+    const int parity = (int)(h->t & 1);
+    const stg_tile keep = h->tile;
+    h->tile = tile;
+    stg::StepArgs a = step_args(h, parity);
+    h->tile = keep;
+    a.stats_every = 0;  // the boundary kernel samples on its own otherwise
+    return stg::launch_step(a, h->d.storage, h->d.collision, false, h->has_tmap ? h->tmap[parity] : nullptr, s,
+                            h->side, h->ev_fork, h->ev_join);
+}
+
+int apply_tile(stg_lbm *h, const stg_tile &tile)
+{
+    if (!tile_ok(tile)) return fail(h, STG_ERR_INVALID, "tile: layout 0 or 1, z chunks 0 or >= 4");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    const stg_tile old = h->tile;
+    h->tile = tile;
+    h->tile.pad0 = 0;
+    rc = capture_all(h);
+    if (rc) {
+        h->tile = old;
+        capture_all(h);
+    }
+    return rc;
+}
+
+const stg_tile *tile_candidates(int *n)
+{
+    static const stg_tile cand[] = {{1, 4, 24, 0},  {1, 6, 24, 0},  {1, 8, 24, 0},  {1, 12, 24, 0}, {1, 16, 24, 0},
+                                    {1, 8, 8, 0},   {0, 16, 24, 0}, {0, 24, 24, 0}, {0, 48, 24, 0}, {0, 0, 0, 0}};
+    *n = (int)(sizeof cand / sizeof cand[0]);
+    return cand;
+}
+
+}  // namespace host
+}  // namespace stg
+
+extern "C" {
+
 int stg_lbm_autotune(stg_lbm *h, int32_t trial_passes, stg_tile *chosen)
 {
     if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
+    if (h->batch) return fail(h, STG_ERR_INVALID, "the lattice is in a batch; tune the batch");
     if (trial_passes < 1 || trial_passes > 1000) return fail(h, STG_ERR_INVALID, "trial_passes must be in [1, 1000]");
     if (h->sticky) return fail(h, h->sticky, "an earlier check failed; reset the state first");
-    static const stg_tile cand[] = {{1, 4, 24, 0},  {1, 6, 24, 0},  {1, 8, 24, 0},  {1, 12, 24, 0}, {1, 16, 24, 0},
-                                    {1, 8, 8, 0},   {0, 16, 24, 0}, {0, 24, 24, 0}, {0, 48, 24, 0}, {0, 0, 0, 0}};
+    int ncand = 0;
+    const stg_tile *cand = tile_candidates(&ncand);
     int rc = wait_stream(h);
     if (rc) return rc;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -882,39 +1043,28 @@ int stg_lbm_autotune(stg_lbm *h, int32_t trial_passes, stg_tile *chosen)
     // plain passes from the current state: src = lat[t & 1], dst = lat[(t & 1) ^ 1];
     // the pass writes the device counter t[p ^ 1] = t + 1, which the next real
     // step writes again, and the mass slots, which every pass rewrites
-    const int parity = (int)(h->t & 1);
-    const stg_tile keep = h->tile;
-    stg_tile best = keep;
+    stg_tile best = h->tile;
     float best_ms = -1.f;
-    for (const stg_tile &c : cand) {
-        h->tile = c;
-        stg::StepArgs a = step_args(h, parity);
-        a.stats_every = 0;  // the boundary kernel samples on its own otherwise
+    for (int c = 0; c < ncand && rc == STG_OK; ++c) {
         cudaError_t e = cudaSuccess;
         for (int k = 0; k <= trial_passes && e == cudaSuccess; ++k) {
             if (k == 1) e = cudaEventRecord(e0, h->stream);
-            if (e == cudaSuccess)
-                e = stg::launch_step(a, h->d.storage, h->d.collision, false, h->has_tmap ? h->tmap[parity] : nullptr,
-                                     h->stream, h->side, h->ev_fork, h->ev_join);
+            if (e == cudaSuccess) e = trial_pass(h, cand[c], h->stream);
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(h, e, "autotune pass");
-            break;
-        }
-        if (best_ms < 0.f || ms < best_ms) {
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "autotune pass");
+        else if (best_ms < 0.f || ms < best_ms) {
             best_ms = ms;
-            best = c;
+            best = cand[c];
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->tile = keep;
     if (rc) return rc;
-    rc = stg_lbm_set_tile(h, &best);
+    rc = apply_tile(h, best);
     if (rc == STG_OK && chosen) *chosen = best;
     return rc;
 }

@@ -27,6 +27,11 @@ struct stg_lbm {
     size_t P = 0, elem = 4;
     void *lat[2] = {nullptr, nullptr};
     float *ubc = nullptr, *uf = nullptr;
+    float *spf = nullptr;  // sponge factor per column (nullptr: no sponge)
+    int n_probes = 0;                     // velocity probes (stg_lbm_set_probes)
+    int *probe_xyz = nullptr;             // device [3 n_probes]
+    float *probe_buf = nullptr;           // device samples of one step_probed call
+    size_t probe_cap = 0;                 // floats in probe_buf
     float *A = nullptr, *B = nullptr, *SQ = nullptr, *sig = nullptr, *a6 = nullptr, *u_int = nullptr;
     double *phi = nullptr, *omg = nullptr;
     int N = 0;
@@ -76,6 +81,16 @@ int poll_check(stg_lbm *h);
 int queue_check_readback(stg_lbm *h, int64_t t_before);
 // wait for h->stream (bounded by the handle's timeout)
 int wait_stream(stg_lbm *h);
+// one plain (non-sampling) step pass from the current state with `tile`, on
+// stream s; it does not advance the step counter, the filter or the
+// statistics (it recomputes what the next real step writes)
+cudaError_t trial_pass(stg_lbm *h, const stg_tile &tile, cudaStream_t s);
+// set the tile and re-capture the handle's own graphs
+int apply_tile(stg_lbm *h, const stg_tile &tile);
+// the autotuner's candidate tiles
+const stg_tile *tile_candidates(int *n);
+// take h out of its batch (batch.cu)
+void batch_detach(stg_lbm *h);
 
 }  // namespace host
 }  // namespace stg

@@ -45,6 +45,7 @@ struct StepArgs {
     float Fx, Fy, Fz;
     int has_force;
     const float *ubc;     // inlet velocity plane [3][nz][ny]
+    const float *spf;     // sponge zone: viscosity factor per column x [nx] (eq. sponge_visco); nullptr: off
     StepCtl *ctl;
     int parity;
     int stats_every, check_every;
@@ -94,6 +95,9 @@ cudaError_t launch_setup_nodes(int ny, int N, const double *R6, const double *le
 cudaError_t launch_init_equilibrium(void *dst, int storage, int nx, int ny, int nz, const float *u_int,
                                     cudaStream_t s);
 cudaError_t launch_mass(const MassArgs &a, cudaStream_t s);
+// velocity of n cells (xyz: device int triples) of a stored lattice into out[3 n]
+cudaError_t launch_probe(const void *src, int storage, size_t P, int nx, int ny, int n, const int *xyz, float Fx,
+                         float Fy, float Fz, float *out, cudaStream_t s);
 
 // TMA-staged interior kernel (tma_kernel.cu): usable when a lattice row is a
 // whole number of 16-byte units; tma_prepare() raises the kernels' dynamic

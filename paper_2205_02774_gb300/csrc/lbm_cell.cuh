@@ -94,9 +94,11 @@ __device__ __forceinline__ void rebuild(float (&g)[Q], float drho, float ux, flo
 // (w = 1/tau_eff here, kf = 1 - w/2).  The 18 moving populations come in
 // opposite pairs, and the edge pairs (a, b, +-) share A_aa + A_bb, so the
 // whole update is a few dozen fused multiply-adds.
-template <bool REG, bool FORCE>
+// SP: sponge zone, eq. (sponge_visco): the cell's viscosity is nu_eff times
+// nuf, i.e. tau = 1/2 + nuf (tau_eff - 1/2).
+template <bool REG, bool FORCE, bool SP = false>
 __device__ __forceinline__ void collide(float (&g)[Q], float tau0, float kq, float Fx, float Fy, float Fz,
-                                        float &rho_o, float &ux_o, float &uy_o, float &uz_o)
+                                        float &rho_o, float &ux_o, float &uy_o, float &uz_o, float nuf = 1.0f)
 {
     float s[9], d[9];
 #pragma unroll
@@ -140,7 +142,8 @@ __device__ __forceinline__ void collide(float (&g)[Q], float tau0, float kq, flo
     const float q2 = nxx * nxx + nyy * nyy + nzz * nzz + 2.0f * (nxy * nxy + nxz * nxz + nyz * nyz);
     const float qh = q2 > 0.f ? sqrtf(q2) : 0.f;
     // eq. (tau_eff), c = 1: tau = tau0/2 + sqrt((tau0 rho)^2 + 18 sqrt2 C Q^1/2)/(2 rho)
-    const float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + kq * qh * irho * irho));
+    float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + kq * qh * irho * irho));
+    if (SP) tau = fmaf(nuf, tau - 0.5f, 0.5f);
     const float om = 1.0f / tau;
     const float uu = ux * ux + uy * uy + uz * uz;
     const float kf = FORCE ? (1.0f - 0.5f * om) : 0.f;  // Guo prefactor

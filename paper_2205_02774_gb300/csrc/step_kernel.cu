@@ -69,7 +69,7 @@ __device__ __forceinline__ void gather_general(const S *__restrict__ src, unsign
 // thread.  EDGE selects the general pull (walls, wraps, inlet/outlet
 // rebuild); the interior variant only sees columns whose x chunk is neither
 // the first nor the last and whose y has both neighbours inside the lattice.
-template <typename S, bool REG, bool FORCE, bool EDGE>
+template <typename S, bool REG, bool FORCE, bool EDGE, bool SP>
 __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
 {
     const S *__restrict__ src = static_cast<const S *>(a.src);
@@ -160,7 +160,7 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
                 }
             }
             float rho, ux, uy, uz;
-            collide<REG, FORCE>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz);
+            collide<REG, FORCE, SP>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz, SP ? __ldg(a.spf + x) : 1.0f);
 #pragma unroll
             for (int i = 0; i < Q; ++i) Pop<S>::st(static_cast<S *>(a.dstp[i]) + here, g[i]);
             if (do_stats) {
@@ -194,10 +194,10 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
 }
 
 // Scalar interior columns: x chunks [il, ir), y = 1..ny-2 (odd nx or narrow lattices).
-template <typename S, bool REG, bool FORCE>
+template <typename S, bool REG, bool FORCE, bool SP>
 __global__ void __launch_bounds__(BX *BZ, 4) lbm_step_kernel(const StepArgs a)
 {
-    step_column<S, REG, FORCE, false>(a, a.il + blockIdx.x, blockIdx.y + 1);
+    step_column<S, REG, FORCE, false, SP>(a, a.il + blockIdx.x, blockIdx.y + 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -324,7 +324,7 @@ struct VecOf {
 // (meaningless) values are neither stored nor counted.  STATS adds the
 // per-cell velocity sums to the block's shared-memory slots.  Returns the
 // thread's sum of rho - 1.
-template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE>
+template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP>
 __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX * VecOf<S>::CPL], int x0, int y,
                                           int zb, int ze, int zs)
 {
@@ -405,7 +405,8 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
 #pragma unroll
             for (int i = 0; i < Q; ++i) g[i] = V::cell(v[i], j);
             float rho, ux, uy, uz;
-            collide<REG, FORCE>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz);
+            collide<REG, FORCE, SP>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz,
+                                    SP && active ? __ldg(a.spf + x + j) : 1.0f);
 #pragma unroll
             for (int i = 0; i < Q; ++i) V::put(v[i], j, g[i]);
             const bool counted = active && !(j == 0 && skip_lo) && !(j == CPL - 1 && skip_hi);
@@ -440,7 +441,7 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
 // the block walks the whole z column, so the per-(x, y) statistics are summed
 // in shared memory without atomics and in a fixed order.  STATS is chosen on
 // the host (it knows the step count); plain steps use lbm_vec_zc_kernel.
-template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE>
+template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP>
 __global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kernel(const StepArgs a)
 {
     constexpr int CPL = VecOf<S>::CPL;
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kerne
 #pragma unroll
             for (int j = 0; j < CPL; ++j) sacc[wi][q][CPL * lane + j] = 0.f;
     }
-    const float sdr = vec_loop<S, REG, FORCE, STATS, YEDGE>(a, sacc, x0, y, wi, a.nz, BZ);
+    const float sdr = vec_loop<S, REG, FORCE, STATS, YEDGE, SP>(a, sacc, x0, y, wi, a.nz, BZ);
     if (STATS) {
         __syncthreads();
         if (wi == 0) {
@@ -497,7 +498,7 @@ struct ZcShape {
     static constexpr int MINB = (LEAN ? 32 : 24) / NW;  // resident blocks per SM
 };
 
-template <typename S, bool REG, bool FORCE, int LAYOUT, bool YEDGE>
+template <typename S, bool REG, bool FORCE, int LAYOUT, bool YEDGE, bool SP>
 __global__ void __launch_bounds__(BX *ZcShape<LAYOUT, REG && !FORCE>::NW, ZcShape<LAYOUT, REG && !FORCE>::MINB)
     lbm_vec_zc_kernel(const StepArgs a)
 {
@@ -511,8 +512,10 @@ __global__ void __launch_bounds__(BX *ZcShape<LAYOUT, REG && !FORCE>::NW, ZcShap
     const long long t = a.ctl->t[a.parity];
     const bool do_check = a.check_every > 0 && ((t + 1) % a.check_every) == 0;
     float sdr;
-    if (LAYOUT == 0) sdr = vec_loop<S, REG, FORCE, false, YEDGE>(a, nullptr, BX * CPL * blockIdx.x, y, zb + wi, ze, NW);
-    else sdr = vec_loop<S, REG, FORCE, false, YEDGE>(a, nullptr, BX * CPL * (NW * blockIdx.x + wi), y, zb, ze, 1);
+    if (LAYOUT == 0)
+        sdr = vec_loop<S, REG, FORCE, false, YEDGE, SP>(a, nullptr, BX * CPL * blockIdx.x, y, zb + wi, ze, NW);
+    else
+        sdr = vec_loop<S, REG, FORCE, false, YEDGE, SP>(a, nullptr, BX * CPL * (NW * blockIdx.x + wi), y, zb, ze, 1);
     if (do_check) mass_finish<BX * NW>(a, sdr);
     if (YEDGE && a.bump_t && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && wi == 0)
         a.ctl->t[a.parity ^ 1] = t + 1;
@@ -522,7 +525,7 @@ __global__ void __launch_bounds__(BX *ZcShape<LAYOUT, REG && !FORCE>::NW, ZcShap
 // one cell per thread through the general pull and the regularized rebuild.
 constexpr int XB_THREADS = 128;
 
-template <typename S, bool REG, bool FORCE>
+template <typename S, bool REG, bool FORCE, bool SP>
 __global__ void __launch_bounds__(XB_THREADS) lbm_xbound_kernel(const StepArgs a)
 {
     __shared__ float red[9][XB_THREADS];
@@ -587,7 +590,7 @@ __global__ void __launch_bounds__(XB_THREADS) lbm_xbound_kernel(const StepArgs a
             rebuild<-1>(g, 0.0f, jx * ir, jy * ir, jz * ir);
         }
         float rho, ux, uy, uz;
-        collide<REG, FORCE>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz);
+        collide<REG, FORCE, SP>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz, SP ? __ldg(a.spf + x) : 1.0f);
 #pragma unroll
         for (int i = 0; i < Q; ++i) Pop<S>::st(static_cast<S *>(a.dstp[i]) + here, g[i]);
         acc[0] += ux; acc[1] += uy; acc[2] += uz;
@@ -614,7 +617,7 @@ __global__ void __launch_bounds__(XB_THREADS) lbm_xbound_kernel(const StepArgs a
 // every chunk of rows 0 and ny-1, and the chunks outside [il, ir) of rows
 // 1..ny-2.  Block 0 also advances the device step counter (read by the next
 // step only).
-template <typename S, bool REG, bool FORCE>
+template <typename S, bool REG, bool FORCE, bool SP>
 __global__ void __launch_bounds__(BX *BZ, 2) lbm_edge_kernel(const StepArgs a)
 {
     const int nxc = (a.nx + BX - 1) / BX;
@@ -632,7 +635,7 @@ __global__ void __launch_bounds__(BX *BZ, 2) lbm_edge_kernel(const StepArgs a)
         bx = k < a.il ? k : a.ir + (k - a.il);
     }
     const long long t = a.ctl->t[a.parity];
-    step_column<S, REG, FORCE, true>(a, bx, y);
+    step_column<S, REG, FORCE, true, SP>(a, bx, y);
     if (a.bump_t && b == 0 && threadIdx.x == 0 && threadIdx.y == 0) a.ctl->t[a.parity ^ 1] = t + 1;
 }
 
@@ -678,7 +681,7 @@ static Split split_of(const StepArgs &a, int cpl)
     return sp;
 }
 
-template <typename S, bool REG, bool FORCE>
+template <typename S, bool REG, bool FORCE, bool SP>
 static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *tmap, cudaStream_t s,
                           cudaStream_t side)
 {
@@ -714,16 +717,16 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
         ab.slot_base = n_in + n_edge;
         ae.bump_t = 1;
         if (n_in > 0) {
-            if (stats) lbm_vec_kernel<S, REG, FORCE, true, false><<<gi, block, 0, s>>>(ai);
-            else if (a.tile_layout == 1) lbm_vec_zc_kernel<S, REG, FORCE, 1, false><<<gi, bi, 0, s>>>(ai);
-            else lbm_vec_zc_kernel<S, REG, FORCE, 0, false><<<gi, bi, 0, s>>>(ai);
+            if (stats) lbm_vec_kernel<S, REG, FORCE, true, false, SP><<<gi, block, 0, s>>>(ai);
+            else if (a.tile_layout == 1) lbm_vec_zc_kernel<S, REG, FORCE, 1, false, SP><<<gi, bi, 0, s>>>(ai);
+            else lbm_vec_zc_kernel<S, REG, FORCE, 0, false, SP><<<gi, bi, 0, s>>>(ai);
         }
-        if (stats) lbm_vec_kernel<S, REG, FORCE, true, true><<<ge, block, 0, side>>>(ae);
-        else lbm_vec_zc_kernel<S, REG, FORCE, 0, true><<<ge, block, 0, side>>>(ae);
-        if (n_xb > 0) lbm_xbound_kernel<S, REG, FORCE><<<dim3(2, ny), XB_THREADS, 0, side>>>(ab);
+        if (stats) lbm_vec_kernel<S, REG, FORCE, true, true, SP><<<ge, block, 0, side>>>(ae);
+        else lbm_vec_zc_kernel<S, REG, FORCE, 0, true, SP><<<ge, block, 0, side>>>(ae);
+        if (n_xb > 0) lbm_xbound_kernel<S, REG, FORCE, SP><<<dim3(2, ny), XB_THREADS, 0, side>>>(ab);
         return;
     }
-    const bool tma = a.interior == 3 && tmap && sp.gx > 0 && sp.gy > 0 && (sp.ir - sp.il) % 2 == 0 &&
+    const bool tma = !SP && a.interior == 3 && tmap && sp.gx > 0 && sp.gy > 0 && (sp.ir - sp.il) % 2 == 0 &&
                      a.nx % 2 == 0 && 19.0 * a.nx * a.ny * a.nz < 4294967296.0 && tma_usable(a.nx, storage);
     const int n_in = sp.gy > 0 ? (tma ? (sp.ir - sp.il) / 2 : sp.gx) * sp.gy : 0;
     a.il = sp.il;
@@ -733,10 +736,10 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
     ai.slot_base = 0;
     ae.slot_base = n_in;
     ae.bump_t = 1;
-    lbm_edge_kernel<S, REG, FORCE><<<sp.n_edge, block, 0, side>>>(ae);
+    lbm_edge_kernel<S, REG, FORCE, SP><<<sp.n_edge, block, 0, side>>>(ae);
     if (n_in > 0) {
         if (tma) launch_tma(ai, tmap, (sp.ir - sp.il) / 2, sp.gy, storage, REG ? 0 : 1, stats, s);
-        else lbm_step_kernel<S, REG, FORCE><<<dim3(sp.gx, sp.gy), block, 0, s>>>(ai);
+        else lbm_step_kernel<S, REG, FORCE, SP><<<dim3(sp.gx, sp.gy), block, 0, s>>>(ai);
     }
 }
 
@@ -746,8 +749,10 @@ static void launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaS
     const Split sp = split_of(a0, VecOf<S>::CPL);
     StepArgs a = a0;
     a.bump_t = 0;
-    if (a.has_force) launch_forced<S, REG, true>(a, sp, stats, tmap, s, side);
-    else launch_forced<S, REG, false>(a, sp, stats, tmap, s, side);
+    // the sponge is only compiled for unforced lattices (the host refuses a sponge with a force)
+    if (a.spf) launch_forced<S, REG, false, true>(a, sp, stats, tmap, s, side);
+    else if (a.has_force) launch_forced<S, REG, true, false>(a, sp, stats, tmap, s, side);
+    else launch_forced<S, REG, false, false>(a, sp, stats, tmap, s, side);
 }
 
 // One fused step pass.  With a side stream and two events the edge work runs
