@@ -187,6 +187,16 @@ int stg_lbm_stats(stg_lbm *h, stg_stats *out);
 int stg_lbm_get_state(stg_lbm *h, void *host, size_t bytes);
 int stg_lbm_set_state(stg_lbm *h, const void *host, size_t bytes, int64_t step);
 
+/* Checkpoint / resume: the whole evolving state (current populations, step
+ * counter, inlet filter state and restart step, FP64 statistics sums and
+ * sample origin, reference mass) as one host image of stg_lbm_checkpoint_bytes
+ * bytes.  Loading it into a lattice created with the same domain and inputs
+ * continues the run bit-identically.  load() refuses an image of another
+ * lattice size or storage.  Errors: STG_ERR_INVALID, STG_ERR_CUDA. */
+int stg_lbm_checkpoint_bytes(const stg_lbm *h, size_t *bytes);
+int stg_lbm_save(stg_lbm *h, void *host, size_t bytes);
+int stg_lbm_load(stg_lbm *h, const void *host, size_t bytes);
+
 /* Copy a sub-block of the current populations (storage format) to host
  * memory: cells x0..x0+bx-1, y0.., z0.., layout [19][bz][by][bx].  The block
  * must lie inside the lattice.  Errors: STG_ERR_INVALID, STG_ERR_CUDA. */

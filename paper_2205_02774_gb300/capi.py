@@ -104,6 +104,9 @@ _SIGNATURES = {
     "stg_lbm_set_tile": (C.c_int, [C.c_void_p, C.POINTER(stg_tile)]),
     "stg_lbm_get_tile": (C.c_int, [C.c_void_p, C.POINTER(stg_tile)]),
     "stg_lbm_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(stg_tile)]),
+    "stg_lbm_checkpoint_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "stg_lbm_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "stg_lbm_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "stg_lbm_get_block": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                     C.c_void_p]),
     "stg_lbm_set_probes": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
@@ -341,3 +344,16 @@ def stg_lbm_get_block(h, x0, y0, z0, out):
     """out: host array [19][bz][by][bx] of the storage dtype."""
     _, bz, by, bx = out.shape
     return _check(lib().stg_lbm_get_block(h, x0, y0, z0, bx, by, bz, C.c_void_p(out.ctypes.data)), h)
+
+
+def stg_lbm_save(h):
+    n = C.c_size_t()
+    _check(lib().stg_lbm_checkpoint_bytes(h, C.byref(n)), h)
+    out = np.empty(n.value, dtype=np.uint8)
+    _check(lib().stg_lbm_save(h, C.c_void_p(out.ctypes.data), out.nbytes), h)
+    return out
+
+
+def stg_lbm_load(h, image):
+    image = np.ascontiguousarray(image, dtype=np.uint8)
+    return _check(lib().stg_lbm_load(h, C.c_void_p(image.ctypes.data), image.nbytes), h)

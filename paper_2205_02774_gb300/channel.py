@@ -159,6 +159,13 @@ class Channel:
         A.stg_lbm_get_state(self.h, out)
         return out
 
+    def save(self):
+        """Checkpoint image (numpy uint8) of the whole evolving state."""
+        return A.stg_lbm_save(self.h)
+
+    def load(self, image):
+        A.stg_lbm_load(self.h, image)
+
     def get_block(self, x0, y0, z0, bx, by, bz):
         """Sub-block [19][bz][by][bx] of the current populations (storage format)."""
         out = np.empty((19, bz, by, bx), dtype=self.state_dtype)

@@ -866,6 +866,107 @@ int stg_lbm_set_state(stg_lbm *h, const void *host, size_t bytes, int64_t step)
     return compute_mass(h, &h->mass0);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Checkpoint image: header, current populations, inlet filter state, FP64
+// statistics sums.
+struct CkptHeader {
+    char magic[8];
+    int32_t nx, ny, nz, storage;
+    int64_t t, t0_stats, t0_filter;
+    double mass0;
+    int64_t pop_bytes, uf_bytes, stat_bytes;
+    int64_t reserved[6];
+};
+static_assert(sizeof(CkptHeader) == 128, "checkpoint header layout");
+constexpr char kCkptMagic[8] = {'S', 'T', 'G', 'C', 'K', 'P', 'T', '1'};
+
+size_t ckpt_bytes(const stg_lbm *h)
+{
+    return sizeof(CkptHeader) + 19 * h->P * h->elem + sizeof(float) * 3 * (size_t)h->d.ny * h->d.nz +
+           sizeof(double) * 9 * (size_t)h->d.nx * h->d.ny;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stg_lbm_checkpoint_bytes(const stg_lbm *h, size_t *bytes)
+{
+    if (!h || !bytes) return STG_ERR_INVALID;
+    *bytes = ckpt_bytes(h);
+    return STG_OK;
+}
+
+int stg_lbm_save(stg_lbm *h, void *host, size_t bytes)
+{
+    if (!h || !host) return fail(h, STG_ERR_INVALID, "NULL argument");
+    if (bytes != ckpt_bytes(h)) return fail(h, STG_ERR_INVALID, "checkpoint size mismatch");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    CkptHeader hd{};
+    std::memcpy(hd.magic, kCkptMagic, 8);
+    hd.nx = h->d.nx;
+    hd.ny = h->d.ny;
+    hd.nz = h->d.nz;
+    hd.storage = h->d.storage;
+    hd.t = h->t;
+    hd.t0_stats = h->t0_stats;
+    StepCtl c{};
+    CK(cudaMemcpy(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost));
+    hd.t0_filter = c.t0_filter;
+    hd.mass0 = h->mass0;
+    hd.pop_bytes = (int64_t)(19 * h->P * h->elem);
+    hd.uf_bytes = (int64_t)(sizeof(float) * 3 * (size_t)h->d.ny * h->d.nz);
+    hd.stat_bytes = (int64_t)(sizeof(double) * 9 * (size_t)h->d.nx * h->d.ny);
+    char *p = static_cast<char *>(host);
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    CK(cudaMemcpy(p, h->lat[h->t & 1], hd.pop_bytes, cudaMemcpyDeviceToHost));
+    p += hd.pop_bytes;
+    CK(cudaMemcpy(p, h->uf, hd.uf_bytes, cudaMemcpyDeviceToHost));
+    p += hd.uf_bytes;
+    const size_t m = (size_t)h->d.nx * h->d.ny;
+    CK(cudaMemcpy(p, h->stat_mean, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(p + sizeof(double) * 3 * m, h->stat_rey, sizeof(double) * 6 * m, cudaMemcpyDeviceToHost));
+    return STG_OK;
+}
+
+int stg_lbm_load(stg_lbm *h, const void *host, size_t bytes)
+{
+    if (!h || !host) return fail(h, STG_ERR_INVALID, "NULL argument");
+    if (h->batch) return fail(h, STG_ERR_INVALID, "the lattice is in a batch; remove it first");
+    if (bytes != ckpt_bytes(h)) return fail(h, STG_ERR_INVALID, "checkpoint size mismatch");
+    CkptHeader hd{};
+    std::memcpy(&hd, host, sizeof hd);
+    if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.nx != h->d.nx || hd.ny != h->d.ny || hd.nz != h->d.nz ||
+        hd.storage != h->d.storage || hd.t < 0 || hd.t0_stats < 0 || hd.t0_stats > hd.t || hd.t0_filter < 0 ||
+        hd.t0_filter > hd.t)
+        return fail(h, STG_ERR_INVALID, "checkpoint does not match this lattice");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    rc = reset_counters(h, hd.t);
+    if (rc) return rc;
+    const char *p = static_cast<const char *>(host) + sizeof hd;
+    CK(cudaMemcpy(h->lat[hd.t & 1], p, hd.pop_bytes, cudaMemcpyHostToDevice));
+    p += hd.pop_bytes;
+    CK(cudaMemcpy(h->uf, p, hd.uf_bytes, cudaMemcpyHostToDevice));
+    p += hd.uf_bytes;
+    const size_t m = (size_t)h->d.nx * h->d.ny;
+    CK(cudaMemcpy(h->stat_mean, p, sizeof(double) * 3 * m, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->stat_rey, p + sizeof(double) * 3 * m, sizeof(double) * 6 * m, cudaMemcpyHostToDevice));
+    StepCtl c{};
+    c.t[hd.t & 1] = hd.t;
+    c.t[(hd.t + 1) & 1] = hd.t;
+    c.t0_filter = hd.t0_filter;
+    CK(cudaMemcpy(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice));
+    h->t0_stats = hd.t0_stats;
+    h->mass0 = hd.mass0;
+    return STG_OK;
+}
+
 int stg_lbm_get_block(stg_lbm *h, int32_t x0, int32_t y0, int32_t z0, int32_t bx, int32_t by, int32_t bz, void *host)
 {
     if (!h || !host) return fail(h, STG_ERR_INVALID, "NULL argument");
