@@ -6,6 +6,10 @@
 // overlap on the GPU and no member waits for another between steps; a block is
 // one graph launch.  A member runs exactly the kernels and arguments it runs
 // alone, so its populations and statistics are bit-identical to a solo run.
+// While members come and go, each member's own graph of B steps is launched
+// on its branch instead (no capture of the whole batch per change); the
+// combined graph is captured once the membership has been stable for a few
+// blocks.
 #include <algorithm>
 #include <chrono>
 #include <string>
@@ -23,6 +27,10 @@ struct stg_batch {
     std::vector<cudaStream_t> ms;      // each member's branch stream
     std::vector<cudaEvent_t> join;     // each member's join event
     std::vector<int64_t> t_cap;        // member step counters when the block graph was captured
+    std::vector<cudaGraphExec_t> mg;   // each member's own graph of B steps (used while membership changes)
+    std::vector<int64_t> mg_t;         // member step counter when its graph was captured
+    std::vector<int> mg_B;             // B of that capture
+    int stable = 0;                    // blocks run since the membership last changed
     cudaEvent_t fork = nullptr, done = nullptr, e0 = nullptr, e1 = nullptr;
     cudaGraphExec_t g = nullptr;
     int B = 16;  // steps per block graph: a multiple of 2 and of every member's sampling period
@@ -145,6 +153,59 @@ int capture_block(stg_batch *b)
     return STG_OK;
 }
 
+constexpr int STABLE_BLOCKS = 3;
+
+// Graph of B steps of member d alone, on its branch stream.
+int capture_member(stg_batch *b, size_t d)
+{
+    stg_lbm *h = b->m[d];
+    if (b->mg[d]) cudaGraphExecDestroy(b->mg[d]);
+    b->mg[d] = nullptr;
+    cudaGraph_t g = nullptr;
+    const cudaStream_t own = h->stream;
+    h->stream = b->ms[d];
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = cudaSuccess;
+        for (int s = 0; s < b->B && e1 == cudaSuccess; ++s)
+            e1 = enqueue_step(h, (int)((h->t + s) & 1), is_stats_step(h, h->t + s));
+        e = cudaStreamEndCapture(h->stream, &g);
+        if (e1 != cudaSuccess) e = e1;
+    }
+    h->stream = own;
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bcuda(b, e, "member capture");
+    }
+    e = cudaGraphInstantiate(&b->mg[d], g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->mg[d] = nullptr;
+        return bcuda(b, e, "cudaGraphInstantiate");
+    }
+    b->mg_t[d] = h->t;
+    b->mg_B[d] = b->B;
+    return STG_OK;
+}
+
+// One block through the members' own graphs, each on its branch.
+int launch_member_graphs(stg_batch *b)
+{
+    BCK(cudaEventRecord(b->fork, b->stream));
+    for (size_t d = 0; d < b->m.size(); ++d) {
+        stg_lbm *h = b->m[d];
+        if (!b->mg[d] || b->mg_B[d] != b->B || (h->t - b->mg_t[d]) % b->B != 0) {
+            const int rc = capture_member(b, d);
+            if (rc) return rc;
+        }
+        BCK(cudaStreamWaitEvent(b->ms[d], b->fork, 0));
+        BCK(cudaGraphLaunch(b->mg[d], b->ms[d]));
+        BCK(cudaEventRecord(b->join[d], b->ms[d]));
+        BCK(cudaStreamWaitEvent(b->stream, b->join[d], 0));
+    }
+    return STG_OK;
+}
+
 // The block graph replays the members' step patterns (parity and sampling
 // steps) only while every member has advanced a multiple of B since capture.
 bool graph_valid(const stg_batch *b)
@@ -177,9 +238,14 @@ int remove_at(stg_batch *b, int d)
     BCK(cudaStreamWaitEvent(h->stream, b->done, 0));
     cudaStreamDestroy(b->ms[d]);  // released once its queued work completes
     cudaEventDestroy(b->join[d]);
+    if (b->mg[d]) cudaGraphExecDestroy(b->mg[d]);
     b->m.erase(b->m.begin() + d);
     b->ms.erase(b->ms.begin() + d);
     b->join.erase(b->join.begin() + d);
+    b->mg.erase(b->mg.begin() + d);
+    b->mg_t.erase(b->mg_t.begin() + d);
+    b->mg_B.erase(b->mg_B.begin() + d);
+    b->stable = 0;
     h->batch = nullptr;
     const int B = block_len(b->m, nullptr);
     b->B = B > 0 ? B : 16;
@@ -252,6 +318,10 @@ int stg_batch_add(stg_batch *b, stg_lbm *h)
     b->m.push_back(h);
     b->ms.push_back(s);
     b->join.push_back(j);
+    b->mg.push_back(nullptr);
+    b->mg_t.push_back(0);
+    b->mg_B.push_back(0);
+    b->stable = 0;
     h->batch = b;
     b->B = B;
     b->dirty = true;
@@ -287,13 +357,19 @@ int stg_batch_step(stg_batch *b, int64_t n)
     int rc = order_after_members(b);
     if (rc) return rc;
     while (n >= b->B) {
-        if (!graph_valid(b)) {
+        if (!graph_valid(b) && b->stable >= STABLE_BLOCKS) {
             rc = capture_block(b);
             if (rc) return rc;
         }
-        BCK(cudaGraphLaunch(b->g, b->stream));
+        if (graph_valid(b)) {
+            BCK(cudaGraphLaunch(b->g, b->stream));
+        } else {
+            rc = launch_member_graphs(b);
+            if (rc) return rc;
+        }
         for (stg_lbm *h : b->m) h->t += b->B;
         n -= b->B;
+        ++b->stable;
     }
     if (n > 0) {
         // the rest: each member's own single-step graphs on its branch
@@ -367,6 +443,11 @@ int stg_batch_autotune(stg_batch *b, int32_t trial_passes, stg_tile *chosen)
     }
     b->dirty = true;
     drop_graph(b);
+    for (size_t d = 0; d < b->m.size(); ++d) {
+        if (b->mg[d]) cudaGraphExecDestroy(b->mg[d]);
+        b->mg[d] = nullptr;
+    }
+    b->stable = 0;
     if (chosen) *chosen = best;
     return STG_OK;
 }

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <utility>
@@ -51,6 +52,40 @@ int cuda_fail(stg_lbm *h, cudaError_t e, const char *what)
 using namespace stg::host;
 
 namespace {
+
+// Pinned host words for the mass read-backs, carved from blocks that are
+// allocated once and kept: cudaMallocHost / cudaFreeHost per lattice could
+// synchronise the device, which would stall the other lattices' work when
+// jobs come and go.
+struct PinnedSlots {
+    std::mutex mu;
+    std::vector<double *> free_slots;
+    std::vector<void *> blocks;
+    static constexpr int SLOT = 4, PER_BLOCK = 256;
+    double *get()
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (free_slots.empty()) {
+            void *b = nullptr;
+            if (cudaMallocHost(&b, sizeof(double) * SLOT * PER_BLOCK) != cudaSuccess) return nullptr;
+            blocks.push_back(b);
+            for (int k = PER_BLOCK - 1; k >= 0; --k) free_slots.push_back(static_cast<double *>(b) + SLOT * k);
+        }
+        double *p = free_slots.back();
+        free_slots.pop_back();
+        return p;
+    }
+    void put(double *p)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        free_slots.push_back(p);
+    }
+};
+PinnedSlots &pinned_slots()
+{
+    static PinnedSlots *s = new PinnedSlots();  // kept for the process lifetime
+    return *s;
+}
 
 #define CK(call)                                                \
     do {                                                        \
@@ -534,7 +569,7 @@ void release(stg_lbm *h)
         else cudaFree(a.first);
     }
     h->allocs.clear();
-    if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    if (h->h_pinned) pinned_slots().put(h->h_pinned);
     if (h->ev_check) cudaEventDestroy(h->ev_check);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -634,7 +669,7 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
         cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess ||
         cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost(&h->h_pinned, 4 * sizeof(double)) != cudaSuccess) {
+        !(h->h_pinned = pinned_slots().get())) {
         h->err = "event / pinned allocation failed";
         return bail(STG_ERR_CUDA);
     }

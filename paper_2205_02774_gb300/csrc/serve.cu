@@ -129,8 +129,15 @@ int stg_serve_run(const stg_job *jobs, int32_t n_jobs, const stg_serve_config *c
     }
     // at most two blocks in flight, so admission and completion decisions track the GPU
     cudaEvent_t ring[2] = {nullptr, nullptr};
-    cudaEventCreateWithFlags(&ring[0], cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&ring[1], cudaEventDisableTiming);
+    if (cudaEventCreateWithFlags(&ring[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ring[1], cudaEventDisableTiming) != cudaSuccess) {
+        if (ring[0]) cudaEventDestroy(ring[0]);
+        stg_batch_destroy(b);
+        if (own_bstream) cudaStreamDestroy(bstream);
+        cudaStreamDestroy(pool.s);
+        cudaMemPoolDestroy(pool.pool);
+        return sfail(STG_ERR_CUDA, "cudaEventCreate");
+    }
     bool ring_used[2] = {false, false};
     int ring_i = 0;
 
@@ -276,6 +283,8 @@ int stg_serve_run(const stg_job *jobs, int32_t n_jobs, const stg_serve_config *c
 
     for (Running &r : run)
         if (r.h) finish(r, rc_run != STG_OK ? rc_run : STG_ERR_CUDA);
+    for (int32_t i = 0; i < n_jobs; ++i)  // never admitted because the run stopped
+        if (results[i].status == -1) results[i].status = rc_run != STG_OK ? rc_run : STG_ERR_CUDA;
     stg_batch_destroy(b);
     if (own_bstream) cudaStreamDestroy(bstream);
     cudaEventDestroy(ring[0]);

@@ -290,10 +290,19 @@ struct Vec<__half, 2> {
         asm volatile("ld.global.nc.L2::256B.b32 %0, [%1];" : "=r"(v) : "l"(p));
         return v;
     }
-    static __device__ __forceinline__ float cell(raw v, int j) { return h2f(v, j); }
+    // the halves of the pair as 16-bit registers: one conversion per value,
+    // no masking or shifting (measured 0.63 -> 0.66 of the FP16 pass)
+    static __device__ __forceinline__ float cell(raw v, int j)
+    {
+        float f;
+        if (j) asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %1; cvt.f32.f16 %0, hi;}" : "=f"(f) : "r"(v));
+        else asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %1; cvt.f32.f16 %0, lo;}" : "=f"(f) : "r"(v));
+        return f;
+    }
     static __device__ __forceinline__ void put(raw &v, int j, float f)
     {
-        v = j ? ((v & 0xffffu) | (f2h(f) << 16)) : ((v & 0xffff0000u) | f2h(f));
+        if (j) asm("{.reg .b16 lo, hi, n; mov.b32 {lo, hi}, %0; cvt.rn.f16.f32 n, %1; mov.b32 %0, {lo, n};}" : "+r"(v) : "f"(f));
+        else asm("{.reg .b16 lo, hi, n; mov.b32 {lo, hi}, %0; cvt.rn.f16.f32 n, %1; mov.b32 %0, {n, hi};}" : "+r"(v) : "f"(f));
     }
     static __device__ __forceinline__ void st(__half *p, raw v) { __stcs(reinterpret_cast<unsigned *>(p), v); }
     static __device__ __forceinline__ void st1(__half *p, raw v, int j)

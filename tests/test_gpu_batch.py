@@ -84,7 +84,7 @@ def test_batch_autotune_and_member_rules():
     from paper_2205_02774_gb300.channel import Channel
     from paper_2205_02774_gb300.serving import Batch
     cs = _cases()[:2]
-    refs = [_alone(c, 44) for c in cs]
+    refs = [_alone(c, 124) for c in cs]
     chans = [Channel.from_case(c, check_every=6, mass_tol=0.5) for c in cs]
     b = Batch()
     for ch in chans:
@@ -100,7 +100,7 @@ def test_batch_autotune_and_member_rules():
             ch.set_tile(1, 8, 24)
         with pytest.raises(StgError):
             ch.set_state(ch.get_state(), 0)
-    b.step(40)
+    b.step(120)  # the first blocks after a change run the members' own graphs, later ones the combined graph
     for ch, ref in zip(chans, refs):
         _same(ch.get_state(), ch.stats(), ref)
     chans[1].close()  # destroying a member takes it out of the batch
