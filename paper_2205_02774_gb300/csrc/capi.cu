@@ -377,13 +377,10 @@ namespace host {
 
 cudaError_t enqueue_step(stg_lbm *h, int parity, bool stats)
 {
-    cudaError_t e = cudaSuccess;
-    if (h->inout) {
-        e = stg::launch_inlet(inlet_args(h, parity), h->stream);
-        if (e != cudaSuccess) return e;
-    }
+    const stg::InletArgs in = inlet_args(h, parity);
     return stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, stats,
-                            h->has_tmap ? h->tmap[parity] : nullptr, h->stream, h->side, h->ev_fork, h->ev_join);
+                            h->has_tmap ? h->tmap[parity] : nullptr, h->stream, h->side, h->ev_fork, h->ev_join,
+                            h->inout ? &in : nullptr);
 }
 
 }  // namespace host

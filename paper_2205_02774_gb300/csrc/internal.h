@@ -86,8 +86,10 @@ struct MassArgs {
 // `stats` must be true exactly on sampling steps ((t + 1) % stats_every == 0);
 // the host tracks t and decides.
 // tensor_map: the source lattice's tensor map (nullptr: no TMA-staged kernel)
+// inlet: the step's inlet kernel (NULL: none), launched on the branch ahead of the boundary work
 cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, const void *tensor_map,
-                        cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
+                        cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join,
+                        const InletArgs *inlet = nullptr);
 cudaError_t launch_inlet(const InletArgs &a, cudaStream_t s);
 cudaError_t launch_setup_nodes(int ny, int N, const double *R6, const double *le, const double *leta,
                                const double *lcut, const double *kn, const double *dk, float *a6,

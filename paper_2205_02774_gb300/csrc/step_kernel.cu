@@ -774,9 +774,10 @@ static void launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaS
 
 // One fused step pass.  With a side stream and two events the edge work runs
 // on a forked branch concurrently with the interior (both read only the
-// previous lattice and write disjoint cells); `s` waits for both.
+// previous lattice and write disjoint cells); `s` waits for both.  `inlet`
+// (may be NULL) is the step's inlet kernel, launched first on the branch.
 cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, const void *tmap,
-                        cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
+                        cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, const InletArgs *inlet)
 {
     cudaError_t e = cudaSuccess;
     const bool forked = side != nullptr && fork != nullptr && join != nullptr;
@@ -785,6 +786,9 @@ cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stat
         if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
     }
     cudaStream_t es = forked ? side : s;
+    // the inlet plane is read only by the boundary work on the branch, so the
+    // inlet kernel runs there, ahead of it, while the interior runs beside it
+    if (inlet && (e = launch_inlet(*inlet, es)) != cudaSuccess) return e;
     if (storage == 0) {
         if (collision == 0) launch_typed<float, true>(a, stats, tmap, s, es);
         else launch_typed<float, false>(a, stats, tmap, s, es);
