@@ -385,12 +385,13 @@ static double load(int32_t type, const void *src, size_t ncell, int i, size_t ce
 
 static int wrap(int a, int n) { a %= n; return a < 0 ? a + n : a; }
 
-static void cell_update(const orc_domain *d, int32_t type, const void *src, int x, int y, int z,
-                        const double *u_bc, double *out, double *rho_o, double *u_o)
+/* Pull streaming into cell (x, y, z), eq. (lbe) left side: f_i(x) =
+ * f*_i(x - c_i); half-way bounce-back at the y walls, periodic z (and x, y
+ * when so configured); a source outside an open x end is unknown (NaN). */
+static void pull_cell(const orc_domain *d, int32_t type, const void *src, int x, int y, int z, double *f)
 {
     const int nx = d->nx, ny = d->ny, nz = d->nz;
     const size_t ncell = (size_t)nx * ny * nz;
-    double f[Q19];
     size_t here = ((size_t)z * ny + y) * nx + x;
     for (int i = 0; i < Q19; ++i) {
         int xs = x - CV[i][0], ys = y - CV[i][1], zs = wrap(z - CV[i][2], nz);
@@ -403,18 +404,28 @@ static void cell_update(const orc_domain *d, int32_t type, const void *src, int 
         else if (xs < 0 || xs >= nx) { f[i] = NAN; continue; }
         f[i] = load(type, src, ncell, i, ((size_t)zs * ny + ys) * nx + xs);
     }
+}
+
+static void cell_update(const orc_domain *d, int32_t type, const void *src, int x, int y, int z,
+                        const double *u_bc, double *out, double *rho_o, double *u_o)
+{
+    const int nx = d->nx;
+    double f[Q19];
+    pull_cell(d, type, src, x, y, z, f);
     if (d->bc_x == 0 && x == 0) {
         orc_inlet_reconstruct(f, u_bc, f);
     } else if (d->bc_x == 0 && x == nx - 1) {
-        /* zero-gradient velocity from the stored neighbour column x = nx-2 */
-        size_t nb = ((size_t)z * ny + y) * nx + (nx - 2);
-        double rho = 0.0, j[3] = {0.0, 0.0, 0.0}, uo[3];
+        /* READING (zero gradient): the outlet takes the velocity of its
+         * neighbour x = nx-2 at this step, i.e. the moments of the neighbour's
+         * streamed populations, with the same definition as the collision's
+         * velocity, u = (sum c f + F/2)/rho (eq. momentum). */
+        double g[Q19], rho = 0.0, j[3] = {0.0, 0.0, 0.0}, uo[3];
+        pull_cell(d, type, src, nx - 2, y, z, g);
         for (int i = 0; i < Q19; ++i) {
-            double v = load(type, src, ncell, i, nb);
-            rho += v;
-            for (int a = 0; a < 3; ++a) j[a] += v * CV[i][a];
+            rho += g[i];
+            for (int a = 0; a < 3; ++a) j[a] += g[i] * CV[i][a];
         }
-        for (int a = 0; a < 3; ++a) uo[a] = j[a] / rho;
+        for (int a = 0; a < 3; ++a) uo[a] = (j[a] + 0.5 * d->force[a]) / rho;
         orc_outlet_reconstruct(f, uo, f);
     }
     collide_nu(d, f, out, rho_o, u_o, orc_sponge_factor(d, x));

@@ -76,23 +76,28 @@ def step(pops, dims, order, tau0, C, F, u_bc, bc_x="stg", bc_y="walls", regulari
     nx, ny, nz = dims
     idx = {tuple(int(a) for a in v): i for i, v in enumerate(order)}
     new = [[[[0.0] * nx for _ in range(ny)] for _ in range(nz)] for _ in range(19)]
+
+    def pull(x, y, z):
+        f = {}
+        for v in VEL:
+            xs, ys, zs = x - v[0], y - v[1], (z - v[2]) % nz
+            if bc_y == "walls" and not (0 <= ys < ny):
+                o = tuple(-a for a in v)
+                f[v] = float(pops[idx[o]][z][y][x])
+                continue
+            ys %= ny
+            if bc_x == "periodic":
+                xs %= nx
+            elif not (0 <= xs < nx):
+                f[v] = float("nan")
+                continue
+            f[v] = float(pops[idx[v]][zs][ys][xs])
+        return f
+
     for z in range(nz):
         for y in range(ny):
             for x in range(nx):
-                f = {}
-                for v in VEL:
-                    xs, ys, zs = x - v[0], y - v[1], (z - v[2]) % nz
-                    if bc_y == "walls" and not (0 <= ys < ny):
-                        o = tuple(-a for a in v)
-                        f[v] = float(pops[idx[o]][z][y][x])
-                        continue
-                    ys %= ny
-                    if bc_x == "periodic":
-                        xs %= nx
-                    elif not (0 <= xs < nx):
-                        f[v] = float("nan")
-                        continue
-                    f[v] = float(pops[idx[v]][zs][ys][xs])
+                f = pull(x, y, z)
                 if bc_x == "stg" and x == 0:
                     ub = [float(u_bc[a][z][y]) for a in range(3)]
                     par = sum(f[v] for v in VEL if v[0] == 0)
@@ -100,9 +105,10 @@ def step(pops, dims, order, tau0, C, F, u_bc, bc_x="stg", bc_y="walls", regulari
                     rho_bc = (par + 2 * leaving) / (1 - ub[0])
                     f = rebuild(f, rho_bc, ub, lambda v: v[0] > 0)
                 elif bc_x == "stg" and x == nx - 1:
-                    g = {v: float(pops[idx[v]][z][y][nx - 2]) for v in VEL}
+                    # zero gradient: the velocity of the neighbour x = nx-2 at this step
+                    g = pull(nx - 2, y, z)
                     r = sum(g.values())
-                    uo = [sum(g[v] * v[a] for v in VEL) / r for a in range(3)]
+                    uo = [(sum(g[v] * v[a] for v in VEL) + 0.5 * F[a]) / r for a in range(3)]
                     f = rebuild(f, 1.0, uo, lambda v: v[0] < 0)
                 out = collide(f, tau0, C, F, regularized)
                 for v in VEL:
