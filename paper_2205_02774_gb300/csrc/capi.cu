@@ -1124,7 +1124,7 @@ cudaError_t trial_pass(stg_lbm *h, const stg_tile &tile, cudaStream_t s)
     h->tile = tile;
     stg::StepArgs a = step_args(h, parity);
     h->tile = keep;
-    a.stats_every = 0;  // the boundary kernel samples on its own otherwise
+    a.stats_every = 0;  // the edge kernel samples on its own otherwise
     return stg::launch_step(a, h->d.storage, h->d.collision, false, h->has_tmap ? h->tmap[parity] : nullptr, s,
                             h->side, h->ev_fork, h->ev_join);
 }

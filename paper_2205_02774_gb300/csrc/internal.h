@@ -86,7 +86,7 @@ struct MassArgs {
 // `stats` must be true exactly on sampling steps ((t + 1) % stats_every == 0);
 // the host tracks t and decides.
 // tensor_map: the source lattice's tensor map (nullptr: no TMA-staged kernel)
-// inlet: the step's inlet kernel (NULL: none), launched on the branch ahead of the boundary work
+// inlet: the step's inlet kernel (NULL: none), launched ahead of the pass
 cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, const void *tensor_map,
                         cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join,
                         const InletArgs *inlet = nullptr);

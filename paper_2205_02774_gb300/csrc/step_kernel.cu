@@ -143,18 +143,25 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
                         const float drb = (par + 2.0f * lv + ubx) / (1.0f - ubx);
                         rebuild<1>(g, drb, ubx, uby, ubz);
                     } else {
-                        // zero-gradient velocity from the stored column x = nx-2, rho = 1
-                        const unsigned nb = ((unsigned)z * ny + y) * nx + (nx - 2);
+                        // zero-gradient pressure outlet: rho = 1 and the velocity of the
+                        // neighbour x = nx-2 at this step, from its streamed populations
+                        float gn[Q];
+                        gather_general<S>(src, P, nx, ny, nx - 2, y, z, nx - 3, nx - 1, true, true, ym, yp, ym_w,
+                                          yp_w, zm, zp, ((unsigned)z * ny + y) * nx + (nx - 2), gn);
                         float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
                         for (int i = 0; i < Q; ++i) {
-                            const float v = Pop<S>::ld(src + (size_t)i * P + nb);
-                            r += v;
-                            jx += cx_of(i) * v;
-                            jy += cy_of(i) * v;
-                            jz += cz_of(i) * v;
+                            r += gn[i];
+                            jx += cx_of(i) * gn[i];
+                            jy += cy_of(i) * gn[i];
+                            jz += cz_of(i) * gn[i];
                         }
                         const float ir = 1.0f / (1.0f + r);
+                        if (FORCE) {
+                            jx += 0.5f * Fx;
+                            jy += 0.5f * Fy;
+                            jz += 0.5f * Fz;
+                        }
                         rebuild<-1>(g, 0.0f, jx * ir, jy * ir, jz * ir);
                     }
                 }
@@ -337,10 +344,12 @@ struct VecOf {
 // zb + zs, ... below ze.  YEDGE rows
 // (y = 0 or ny-1) take the y neighbour by half-way bounce-back (walls: the
 // cell's own opposite population) or by the periodic wrap.  In inlet/outlet
-// mode the cells x = 0 and x = nx-1 are left to the boundary kernel: their
-// (meaningless) values are neither stored nor counted.  STATS adds the
-// per-cell velocity sums to the block's shared-memory slots.  Returns the
-// thread's sum of rho - 1.
+// mode the inlet node x = 0 is rebuilt by the regularized Zou-He
+// reconstruction (Sec. III.B) and the outlet node x = nx-1 by the regularized
+// pressure outlet, whose velocity is that of the same lane's previous cell
+// x = nx-2; their pulled values from outside the lattice are never read.
+// STATS adds the per-cell velocity sums to the block's shared-memory slots.
+// Returns the thread's sum of rho - 1.
 template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP>
 __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX * VecOf<S>::CPL], int x0, int y,
                                           int zb, int ze, int zs)
@@ -359,9 +368,11 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
     const bool side_r = active && (lane == 31 || x + CPL == nx);
     const int xl = x == 0 ? (inout ? 0 : nx - 1) : x - 1;        // element read for x-1
     const int xr = x + CPL == nx ? (inout ? nx - 1 : 0) : x + CPL; // element read for x+CPL
-    // cells excluded in inlet/outlet mode (handled by the boundary kernel)
-    const bool skip_lo = inout && x == 0;
-    const bool skip_hi = inout && x + CPL == nx;
+    // inlet/outlet mode: the first lane's first cell is the inlet node x = 0,
+    // the last lane's last cell the outlet node x = nx-1 (nx is a multiple of
+    // CPL); both are rebuilt here from the values already in registers
+    const bool at_inlet = inout && x == 0;
+    const bool at_outlet = inout && active && x + CPL == nx;
     // y neighbours of this row (YEDGE rows only)
     bool ym_bb = false, yp_bb = false;
     int ym_off = nx, yp_off = -nx;  // element offset of the source row for c_y = +1 / -1 (subtracted)
@@ -416,17 +427,40 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
             else if (cx > 0) v[i] = V::shift_left(cur, sbase + (rbase + xl), side_l && !(inout && x == 0));
             else v[i] = V::shift_right(cur, sbase + (rbase + xr), side_r && !(inout && x + CPL == nx));
         }
+        float upx = 0.f, upy = 0.f, upz = 0.f;  // velocity of the lane's previous cell
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
             float g[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) g[i] = V::cell(v[i], j);
+            if (j == 0 && at_inlet) {
+                // Zou-He density, eq. (density_bc): parallel set + 2 x leaving set,
+                // rho_bc - 1 = (S_g + u_x)/(1 - u_x) in shifted variables; the
+                // unknowns (c_x > 0, their sources lie outside) are not read
+                const size_t pc = (size_t)z * ny + y, pl3 = (size_t)ny * nz;
+                const float ubx = a.ubc[pc], uby = a.ubc[pl3 + pc], ubz = a.ubc[2 * pl3 + pc];
+                float par = 0.f, lv = 0.f;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    if (cx_of(i) == 0) par += g[i];
+                    if (cx_of(i) < 0) lv += g[i];
+                }
+                rebuild<1>(g, (par + 2.0f * lv + ubx) / (1.0f - ubx), ubx, uby, ubz);
+            }
+            if (j == CPL - 1 && at_outlet) {
+                // zero-gradient pressure outlet: rho = 1 and the velocity of the
+                // neighbour x = nx-2 (this lane's previous cell) at this step
+                rebuild<-1>(g, 0.0f, upx, upy, upz);
+            }
             float rho, ux, uy, uz;
             collide<REG, FORCE, SP>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz,
                                     SP && active ? __ldg(a.spf + x + j) : 1.0f);
+            upx = ux;
+            upy = uy;
+            upz = uz;
 #pragma unroll
             for (int i = 0; i < Q; ++i) V::put(v[i], j, g[i]);
-            const bool counted = active && !(j == 0 && skip_lo) && !(j == CPL - 1 && skip_hi);
+            const bool counted = active;
             if (STATS && counted) {
                 float *sp = &sacc[wi][0][CPL * lane + j];
                 constexpr int L = BX * CPL;
@@ -437,16 +471,8 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
             if (counted) sdr += rho - 1.0f;
         }
         if (active) {
-            if (!skip_lo && !skip_hi) {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) V::st(dbase + (i * Pv + here), v[i]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < Q; ++i)
-#pragma unroll
-                    for (int j = 0; j < CPL; ++j)
-                        if (!(j == 0 && skip_lo) && !(j == CPL - 1 && skip_hi)) V::st1(dbase + (i * Pv + here), v[i], j);
-            }
+            for (int i = 0; i < Q; ++i) V::st(dbase + (i * Pv + here), v[i]);
         }
     }
     return sdr;
@@ -480,11 +506,10 @@ __global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kerne
         __syncthreads();
         if (wi == 0) {
             const size_t m = (size_t)nx * ny;
-            const bool inout = a.bc_x == 0;
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
                 const int xc = x0 + CPL * lane + j;
-                if (xc >= nx || (inout && (xc == 0 || xc == nx - 1))) continue;
+                if (xc >= nx) continue;
                 const size_t xy = (size_t)y * nx + xc;
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
@@ -507,8 +532,8 @@ __global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kerne
 // grid small.  LAYOUT 0: 8 warps on one 64-cell x chunk, warp w taking the
 // planes w, w + 8, ... of the chunk; LAYOUT 1: 4 warps on 4 consecutive x
 // chunks (256 cells), all walking the chunk's planes together.  The regularized
-// unforced variants fit 64 registers (32 warps per SM); BGK and forced ones
-// get 80 (24 warps per SM).
+// unforced interior variants fit 64 registers (32 warps per SM); BGK, forced
+// and wall-row ones get 80 (24 warps per SM).
 template <int LAYOUT, bool LEAN>
 struct ZcShape {
     static constexpr int NW = LAYOUT == 0 ? BZ : 4;  // warps per block
@@ -516,11 +541,12 @@ struct ZcShape {
 };
 
 template <typename S, bool REG, bool FORCE, int LAYOUT, bool YEDGE, bool SP>
-__global__ void __launch_bounds__(BX *ZcShape<LAYOUT, REG && !FORCE>::NW, ZcShape<LAYOUT, REG && !FORCE>::MINB)
+__global__ void __launch_bounds__(BX *ZcShape<LAYOUT, REG && !FORCE && !YEDGE>::NW,
+                                  ZcShape<LAYOUT, REG && !FORCE && !YEDGE>::MINB)
     lbm_vec_zc_kernel(const StepArgs a)
 {
     constexpr int CPL = VecOf<S>::CPL;
-    constexpr int NW = ZcShape<LAYOUT, REG && !FORCE>::NW;
+    constexpr int NW = ZcShape<LAYOUT, REG && !FORCE && !YEDGE>::NW;
     const int wi = threadIdx.y;
     const int y = YEDGE ? (blockIdx.y == 0 ? 0 : a.ny - 1) : blockIdx.y + 1;
     const int zc0 = YEDGE ? a.tile_wall_zc : a.tile_zc;
@@ -536,98 +562,6 @@ __global__ void __launch_bounds__(BX *ZcShape<LAYOUT, REG && !FORCE>::NW, ZcShap
     if (do_check) mass_finish<BX * NW>(a, sdr);
     if (YEDGE && a.bump_t && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && wi == 0)
         a.ctl->t[a.parity ^ 1] = t + 1;
-}
-
-// Inlet (x = 0) and outlet (x = nx-1) cells: block (side, y), threads over z,
-// one cell per thread through the general pull and the regularized rebuild.
-constexpr int XB_THREADS = 128;
-
-template <typename S, bool REG, bool FORCE, bool SP>
-__global__ void __launch_bounds__(XB_THREADS) lbm_xbound_kernel(const StepArgs a)
-{
-    __shared__ float red[9][XB_THREADS];
-    const S *__restrict__ src = static_cast<const S *>(a.src);
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const unsigned P = a.P;
-    const int x = blockIdx.x == 0 ? 0 : nx - 1;
-    const int y = blockIdx.y;
-    const int tid = threadIdx.x;
-    const long long t = a.ctl->t[a.parity];
-    const bool do_stats = a.stats_every > 0 && ((t + 1) % a.stats_every) == 0;
-    const bool do_check = a.check_every > 0 && ((t + 1) % a.check_every) == 0;
-    const float tau0 = a.tau0, kq = a.kq;
-    const float Fx = a.Fx, Fy = a.Fy, Fz = a.Fz;
-    const int xm = max(x - 1, 0), xp = min(x + 1, nx - 1);
-    const bool xm_ok = x - 1 >= 0, xp_ok = x + 1 < nx;
-    int ym = y - 1, yp = y + 1;
-    bool ym_w = false, yp_w = false;
-    if (a.bc_y == 0) {
-        ym_w = ym < 0;
-        yp_w = yp >= ny;
-        ym = max(ym, 0);
-        yp = min(yp, ny - 1);
-    } else {
-        if (ym < 0) ym += ny;
-        if (yp >= ny) yp -= ny;
-    }
-    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float sdr = 0.f;
-    for (int z = tid; z < nz; z += XB_THREADS) {
-        const int zm = (z == 0) ? nz - 1 : z - 1;
-        const int zp = (z == nz - 1) ? 0 : z + 1;
-        const unsigned here = ((unsigned)z * ny + y) * nx + x;
-        float g[Q];
-        gather_general<S>(src, P, nx, ny, x, y, z, xm, xp, xm_ok, xp_ok, ym, yp, ym_w, yp_w, zm, zp, here, g);
-        if (x == 0) {
-            const size_t pc = (size_t)z * ny + y, pl3 = (size_t)ny * nz;
-            const float ubx = a.ubc[pc], uby = a.ubc[pl3 + pc], ubz = a.ubc[2 * pl3 + pc];
-            // Zou-He density, eq. (density_bc): parallel set + 2 x leaving set.
-            // The weights of that combination sum to 1 (2/3 + 2 x 1/6), so
-            // rho_bc - 1 = (S_g + u_x)/(1 - u_x) with S_g the same sum of g.
-            float par = 0.f, lv = 0.f;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                if (cx_of(i) == 0) par += g[i];
-                if (cx_of(i) < 0) lv += g[i];
-            }
-            rebuild<1>(g, (par + 2.0f * lv + ubx) / (1.0f - ubx), ubx, uby, ubz);
-        } else {
-            // zero-gradient velocity from the stored column x = nx-2, rho = 1
-            const unsigned nb = ((unsigned)z * ny + y) * nx + (nx - 2);
-            float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const float v = Pop<S>::ld(src + (size_t)i * P + nb);
-                r += v;
-                jx += cx_of(i) * v;
-                jy += cy_of(i) * v;
-                jz += cz_of(i) * v;
-            }
-            const float ir = 1.0f / (1.0f + r);
-            rebuild<-1>(g, 0.0f, jx * ir, jy * ir, jz * ir);
-        }
-        float rho, ux, uy, uz;
-        collide<REG, FORCE, SP>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz, SP ? __ldg(a.spf + x) : 1.0f);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) Pop<S>::st(static_cast<S *>(a.dstp[i]) + here, g[i]);
-        acc[0] += ux; acc[1] += uy; acc[2] += uz;
-        acc[3] += ux * ux; acc[4] += uy * uy; acc[5] += uz * uz;
-        acc[6] += ux * uy; acc[7] += ux * uz; acc[8] += uy * uz;
-        sdr += rho - 1.0f;
-    }
-    if (do_stats) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) red[q][tid] = acc[q];
-        __syncthreads();
-        if (tid < 9) {
-            double sum = 0.0;
-            for (int k = 0; k < XB_THREADS; ++k) sum += (double)red[tid][k];
-            const size_t m = (size_t)nx * ny, xy = (size_t)y * nx + x;
-            if (tid < 3) a.stat_mean[tid * m + xy] += sum;
-            else a.stat_rey[(tid - 3) * m + xy] += sum;
-        }
-    }
-    if (do_check) mass_finish<XB_THREADS>(a, sdr);
 }
 
 // Edge columns of the one-cell-per-thread split (32 wide, general pull):
@@ -664,8 +598,8 @@ int step_grid_blocks(int nx, int ny, int nz)
 }
 
 // How a pass covers the lattice.
-//  vector split: vector kernel on rows 1..ny-2 and on rows {0, ny-1} (all x),
-//                boundary kernel on x = 0 and x = nx-1 (inlet/outlet only);
+//  vector split: vector kernel on rows 1..ny-2 and on rows {0, ny-1} (all x,
+//                inlet/outlet nodes included);
 //  scalar split: interior kernel (one cell per thread, or TMA-staged) on the
 //                32-wide chunks [1, nxc-1) of rows 1..ny-2, edge kernel on the
 //                rest.
@@ -726,12 +660,10 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
         }
         const int n_in = rows_in > 0 ? (int)(gi.x * gi.y * gi.z) : 0;
         const int n_edge = (int)(ge.x * ge.y * ge.z);
-        const int n_xb = a.bc_x == 0 ? 2 * ny : 0;
-        a.total_blocks = (unsigned)(n_in + n_edge + n_xb);
-        StepArgs ai = a, ae = a, ab = a;
+        a.total_blocks = (unsigned)(n_in + n_edge);
+        StepArgs ai = a, ae = a;
         ai.slot_base = 0;
         ae.slot_base = n_in;
-        ab.slot_base = n_in + n_edge;
         ae.bump_t = 1;
         if (n_in > 0) {
             if (stats) lbm_vec_kernel<S, REG, FORCE, true, false, SP><<<gi, block, 0, s>>>(ai);
@@ -740,7 +672,6 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
         }
         if (stats) lbm_vec_kernel<S, REG, FORCE, true, true, SP><<<ge, block, 0, side>>>(ae);
         else lbm_vec_zc_kernel<S, REG, FORCE, 0, true, SP><<<ge, block, 0, side>>>(ae);
-        if (n_xb > 0) lbm_xbound_kernel<S, REG, FORCE, SP><<<dim3(2, ny), XB_THREADS, 0, side>>>(ab);
         return;
     }
     const bool tma = !SP && a.interior == 3 && tmap && sp.gx > 0 && sp.gy > 0 && (sp.ir - sp.il) % 2 == 0 &&
@@ -775,20 +706,20 @@ static void launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaS
 // One fused step pass.  With a side stream and two events the edge work runs
 // on a forked branch concurrently with the interior (both read only the
 // previous lattice and write disjoint cells); `s` waits for both.  `inlet`
-// (may be NULL) is the step's inlet kernel, launched first on the branch.
+// (may be NULL) is the step's inlet kernel, launched first.
 cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, const void *tmap,
                         cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, const InletArgs *inlet)
 {
     cudaError_t e = cudaSuccess;
+    // the inlet plane is read by the inlet nodes of both the main launch and
+    // the branch, so the inlet kernel runs first
+    if (inlet && (e = launch_inlet(*inlet, s)) != cudaSuccess) return e;
     const bool forked = side != nullptr && fork != nullptr && join != nullptr;
     if (forked) {
         if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
     }
     cudaStream_t es = forked ? side : s;
-    // the inlet plane is read only by the boundary work on the branch, so the
-    // inlet kernel runs there, ahead of it, while the interior runs beside it
-    if (inlet && (e = launch_inlet(*inlet, es)) != cudaSuccess) return e;
     if (storage == 0) {
         if (collision == 0) launch_typed<float, true>(a, stats, tmap, s, es);
         else launch_typed<float, false>(a, stats, tmap, s, es);
