@@ -188,7 +188,8 @@ int stg_lbm_get_state(stg_lbm *h, void *host, size_t bytes);
 int stg_lbm_set_state(stg_lbm *h, const void *host, size_t bytes, int64_t step);
 
 /* Checkpoint / resume: the whole evolving state (current populations, step
- * counter, inlet filter state and restart step, FP64 statistics sums and
+ * counter, inlet filter state, the current step's inlet plane and the filter's
+ * restart step, FP64 statistics sums and
  * sample origin, reference mass) as one host image of stg_lbm_checkpoint_bytes
  * bytes.  Loading it into a lattice created with the same domain and inputs
  * continues the run bit-identically.  load() refuses an image of another

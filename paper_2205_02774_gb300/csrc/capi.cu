@@ -287,6 +287,12 @@ int build_inlet(stg_lbm *h, const stg_rans_profile *r, uint64_t seed)
     return STG_OK;
 }
 
+// inlet plane of the step with this parity
+float *ubc_plane(const stg_lbm *h, int parity)
+{
+    return h->ubc + (size_t)(parity & 1) * 3 * (size_t)h->d.ny * h->d.nz;
+}
+
 stg::StepArgs step_args(const stg_lbm *h, int parity)
 {
     stg::StepArgs a{};
@@ -313,7 +319,7 @@ stg::StepArgs step_args(const stg_lbm *h, int parity)
     a.Fy = (float)h->d.force[1];
     a.Fz = (float)h->d.force[2];
     a.has_force = (h->d.force[0] != 0.0 || h->d.force[1] != 0.0 || h->d.force[2] != 0.0);
-    a.ubc = h->ubc;
+    a.ubc = ubc_plane(h, parity);
     a.spf = h->spf;
     a.ctl = h->ctl;
     a.parity = parity;
@@ -347,7 +353,8 @@ stg::InletArgs inlet_args(const stg_lbm *h, int parity)
     a.u_int = h->u_int;
     a.a_filter = h->a_filter;
     a.uf = h->uf;
-    a.ubc = h->ubc;
+    a.ubc = ubc_plane(h, parity ^ 1);  // the plane of the next step
+    a.ahead = 1;
     a.ctl = h->ctl;
     a.parity = parity;
     return a;
@@ -547,6 +554,13 @@ int reset_counters(stg_lbm *h, int64_t step)
     CK(cudaMemsetAsync(h->stat_mean, 0, sizeof(double) * 3 * m, h->stream));
     CK(cudaMemsetAsync(h->stat_rey, 0, sizeof(double) * 6 * m, h->stream));
     CK(cudaMemsetAsync(h->mass_out, 0, sizeof(double) * 2, h->stream));
+    if (h->inout) {
+        // the inlet plane of the restart step (later planes are computed one step ahead)
+        stg::InletArgs in = inlet_args(h, (int)(step & 1));
+        in.ubc = ubc_plane(h, (int)(step & 1));
+        in.ahead = 0;
+        CK(stg::launch_inlet(in, h->stream));
+    }
     CK(cudaStreamSynchronize(h->stream));
     h->t = step;
     h->t0_stats = step;
@@ -679,7 +693,7 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
     h->elem = domain->storage == STG_FP32 ? 4 : 2;
     h->lat[0] = dalloc(h, 19 * h->P * h->elem);
     h->lat[1] = dalloc(h, 19 * h->P * h->elem);
-    h->ubc = (float *)dalloc(h, sizeof(float) * 3 * (size_t)ny * nz);
+    h->ubc = (float *)dalloc(h, sizeof(float) * 6 * (size_t)ny * nz);
     h->uf = (float *)dalloc(h, sizeof(float) * 3 * (size_t)ny * nz);
     h->ctl = (StepCtl *)dalloc(h, sizeof(StepCtl));
     h->stat_mean = (double *)dalloc(h, sizeof(double) * 3 * (size_t)nx * ny);
@@ -713,7 +727,7 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
     e = cudaMemsetAsync(h->mass_counter, 0, sizeof(unsigned) * 4, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->m_counter, 0, sizeof(unsigned) * 4, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->mass_out, 0, sizeof(double) * 2, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->ubc, 0, sizeof(float) * 3 * (size_t)ny * nz, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ubc, 0, sizeof(float) * 6 * (size_t)ny * nz, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->uf, 0, sizeof(float) * 3 * (size_t)ny * nz, h->stream);
     if (e != cudaSuccess) {
         cuda_fail(h, e, "cudaMemsetAsync");
@@ -759,7 +773,7 @@ int stg_lbm_estimate_bytes(const stg_domain *d, const stg_params *p, int64_t *by
     auto r = [](double b) { return (double)(((int64_t)std::max(b, 16.0) + 255) & ~int64_t(255)); };
     const double nx = d->nx, ny = d->ny, nz = d->nz, P = nx * ny * nz;
     const double elem = d->storage == STG_FP32 ? 4.0 : 2.0;
-    double b = 2 * r(19 * P * elem) + 2 * r(12 * ny * nz) + r(sizeof(StepCtl)) + r(24 * nx * ny) + r(48 * nx * ny) +
+    double b = 2 * r(19 * P * elem) + r(24 * ny * nz) + r(12 * ny * nz) + r(sizeof(StepCtl)) + r(24 * nx * ny) + r(48 * nx * ny) +
                r(8.0 * stg::step_grid_blocks(d->nx, d->ny, d->nz)) + 2 * r(16) + 2 * r(16) +
                r(8.0 * stg::mass_grid_blocks());
     if (d->bc_x == STG_BC_X_INLET_OUTLET) {
@@ -909,15 +923,15 @@ struct CkptHeader {
     int32_t nx, ny, nz, storage;
     int64_t t, t0_stats, t0_filter;
     double mass0;
-    int64_t pop_bytes, uf_bytes, stat_bytes;
-    int64_t reserved[6];
+    int64_t pop_bytes, uf_bytes, stat_bytes, plane_bytes;
+    int64_t reserved[5];
 };
 static_assert(sizeof(CkptHeader) == 128, "checkpoint header layout");
-constexpr char kCkptMagic[8] = {'S', 'T', 'G', 'C', 'K', 'P', 'T', '1'};
+constexpr char kCkptMagic[8] = {'S', 'T', 'G', 'C', 'K', 'P', 'T', '2'};
 
 size_t ckpt_bytes(const stg_lbm *h)
 {
-    return sizeof(CkptHeader) + 19 * h->P * h->elem + sizeof(float) * 3 * (size_t)h->d.ny * h->d.nz +
+    return sizeof(CkptHeader) + 19 * h->P * h->elem + sizeof(float) * 6 * (size_t)h->d.ny * h->d.nz +
            sizeof(double) * 9 * (size_t)h->d.nx * h->d.ny;
 }
 
@@ -953,6 +967,7 @@ int stg_lbm_save(stg_lbm *h, void *host, size_t bytes)
     hd.pop_bytes = (int64_t)(19 * h->P * h->elem);
     hd.uf_bytes = (int64_t)(sizeof(float) * 3 * (size_t)h->d.ny * h->d.nz);
     hd.stat_bytes = (int64_t)(sizeof(double) * 9 * (size_t)h->d.nx * h->d.ny);
+    hd.plane_bytes = hd.uf_bytes;
     char *p = static_cast<char *>(host);
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
@@ -960,6 +975,8 @@ int stg_lbm_save(stg_lbm *h, void *host, size_t bytes)
     p += hd.pop_bytes;
     CK(cudaMemcpy(p, h->uf, hd.uf_bytes, cudaMemcpyDeviceToHost));
     p += hd.uf_bytes;
+    CK(cudaMemcpy(p, ubc_plane(h, (int)(h->t & 1)), hd.plane_bytes, cudaMemcpyDeviceToHost));  // this step's inlet plane
+    p += hd.plane_bytes;
     const size_t m = (size_t)h->d.nx * h->d.ny;
     CK(cudaMemcpy(p, h->stat_mean, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(p + sizeof(double) * 3 * m, h->stat_rey, sizeof(double) * 6 * m, cudaMemcpyDeviceToHost));
@@ -986,6 +1003,8 @@ int stg_lbm_load(stg_lbm *h, const void *host, size_t bytes)
     p += hd.pop_bytes;
     CK(cudaMemcpy(h->uf, p, hd.uf_bytes, cudaMemcpyHostToDevice));
     p += hd.uf_bytes;
+    CK(cudaMemcpy(ubc_plane(h, (int)(hd.t & 1)), p, hd.plane_bytes, cudaMemcpyHostToDevice));
+    p += hd.plane_bytes;
     const size_t m = (size_t)h->d.nx * h->d.ny;
     CK(cudaMemcpy(h->stat_mean, p, sizeof(double) * 3 * m, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->stat_rey, p + sizeof(double) * 3 * m, sizeof(double) * 6 * m, cudaMemcpyHostToDevice));
@@ -1027,7 +1046,9 @@ int stg_lbm_get_inlet(stg_lbm *h, float *host_u)
     if (!h || !host_u) return fail(h, STG_ERR_INVALID, "NULL argument");
     int rc = wait_stream(h);
     if (rc) return rc;
-    CK(cudaMemcpy(host_u, h->ubc, sizeof(float) * 3 * (size_t)h->d.ny * h->d.nz, cudaMemcpyDeviceToHost));
+    // the plane of the last completed step
+    CK(cudaMemcpy(host_u, ubc_plane(h, (int)((h->t + 1) & 1)), sizeof(float) * 3 * (size_t)h->d.ny * h->d.nz,
+                  cudaMemcpyDeviceToHost));
     return STG_OK;
 }
 
@@ -1035,7 +1056,7 @@ int stg_lbm_device_state(stg_lbm *h, void **pops, float **inlet_u)
 {
     if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
     if (pops) *pops = h->lat[h->t & 1];
-    if (inlet_u) *inlet_u = h->ubc;
+    if (inlet_u) *inlet_u = ubc_plane(h, (int)((h->t + 1) & 1));
     return STG_OK;
 }
 

@@ -26,7 +26,7 @@ struct stg_lbm {
     std::vector<std::pair<void *, size_t>> allocs;
     size_t P = 0, elem = 4;
     void *lat[2] = {nullptr, nullptr};
-    float *ubc = nullptr, *uf = nullptr;
+    float *ubc = nullptr, *uf = nullptr;  // ubc: inlet planes of steps t and t + 1, [2][3][nz][ny] by step parity
     float *spf = nullptr;  // sponge factor per column (nullptr: no sponge)
     int n_probes = 0;                     // velocity probes (stg_lbm_set_probes)
     int *probe_xyz = nullptr;             // device [3 n_probes]

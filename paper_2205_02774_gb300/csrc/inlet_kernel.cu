@@ -12,6 +12,9 @@
 // part phi^n + omega^n t (evaluated in FP64 per block); their FP32 sum is
 // below 6 pi whatever the step count and is reduced to [-pi, pi] before the
 // cosine.  Each block serves 32 nodes; its 8 warps split the mode sum.
+// The plane of step t + 1 is computed during step t (ahead = 1), beside the
+// step pass that reads the plane of step t; the first plane after a reset is
+// computed with ahead = 0.
 #include "internal.h"
 
 namespace stg {
@@ -27,7 +30,7 @@ __global__ void __launch_bounds__(INLET_NODES *INLET_WARPS) stg_inlet_kernel(con
     float *theta = sm;
     float *sig = sm + a.N;
     const int tid = threadIdx.y * INLET_NODES + threadIdx.x;
-    const long long t = a.ctl->t[a.parity];
+    const long long t = a.ctl->t[a.parity] + a.ahead;
     const bool first = (t == a.ctl->t0_filter);
     // time part of the phase, phi^n + omega^n t, reduced to [0, 2 pi) in FP64
     for (int n = tid; n < a.N; n += INLET_NODES * INLET_WARPS) {

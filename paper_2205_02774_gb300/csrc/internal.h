@@ -69,6 +69,7 @@ struct InletArgs {
     float a_filter;
     float *uf;            // [3][nz][ny] filtered fluctuation (state)
     float *ubc;           // [3][nz][ny] inlet velocity output
+    int ahead;            // the plane is for step t + ahead (t = ctl->t[parity])
     StepCtl *ctl;
     int parity;
 };
@@ -86,7 +87,7 @@ struct MassArgs {
 // `stats` must be true exactly on sampling steps ((t + 1) % stats_every == 0);
 // the host tracks t and decides.
 // tensor_map: the source lattice's tensor map (nullptr: no TMA-staged kernel)
-// inlet: the step's inlet kernel (NULL: none), launched ahead of the pass
+// inlet: the inlet kernel for the next step's plane (NULL: none), launched on the branch
 cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, const void *tensor_map,
                         cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join,
                         const InletArgs *inlet = nullptr);

@@ -706,20 +706,20 @@ static void launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaS
 // One fused step pass.  With a side stream and two events the edge work runs
 // on a forked branch concurrently with the interior (both read only the
 // previous lattice and write disjoint cells); `s` waits for both.  `inlet`
-// (may be NULL) is the step's inlet kernel, launched first.
+// (may be NULL) computes the next step's inlet plane on the branch.
 cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, const void *tmap,
                         cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, const InletArgs *inlet)
 {
     cudaError_t e = cudaSuccess;
-    // the inlet plane is read by the inlet nodes of both the main launch and
-    // the branch, so the inlet kernel runs first
-    if (inlet && (e = launch_inlet(*inlet, s)) != cudaSuccess) return e;
     const bool forked = side != nullptr && fork != nullptr && join != nullptr;
     if (forked) {
         if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
     }
     cudaStream_t es = forked ? side : s;
+    // the inlet kernel writes the plane of the next step, which nothing in
+    // this pass reads, so it runs on the branch beside the interior
+    if (inlet && (e = launch_inlet(*inlet, es)) != cudaSuccess) return e;
     if (storage == 0) {
         if (collision == 0) launch_typed<float, true>(a, stats, tmap, s, es);
         else launch_typed<float, false>(a, stats, tmap, s, es);
