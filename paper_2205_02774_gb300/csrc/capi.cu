@@ -331,6 +331,7 @@ stg::StepArgs step_args(const stg_lbm *h, int parity)
     a.check_every = h->d.check_every;
     a.stat_mean = h->stat_mean;
     a.stat_rey = h->stat_rey;
+    a.stat_part = h->stat_part;
     a.mass_partial = h->mass_partial;
     a.mass_counter = h->mass_counter;
     a.mass_out = h->mass_out;
@@ -699,6 +700,13 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
     h->stat_mean = (double *)dalloc(h, sizeof(double) * 3 * (size_t)nx * ny);
     h->stat_rey = (double *)dalloc(h, sizeof(double) * 6 * (size_t)nx * ny);
     h->mass_partial = (double *)dalloc(h, sizeof(double) * stg::step_grid_blocks(nx, ny, nz));
+    if (domain->stats_every > 0) {
+        h->stat_part = (float *)dalloc(h, sizeof(float) * 9 * (size_t)nx * ny * ((nz + stg::STAT_GROUP - 1) / stg::STAT_GROUP));
+        if (!h->stat_part) {
+            h->err = "device allocation failed";
+            return bail(STG_ERR_NOMEM);
+        }
+    }
     h->mass_counter = (unsigned *)dalloc(h, sizeof(unsigned) * 4);
     h->mass_out = (double *)dalloc(h, sizeof(double) * 2);
     h->m_partial = (double *)dalloc(h, sizeof(double) * stg::mass_grid_blocks());
@@ -776,11 +784,12 @@ int stg_lbm_estimate_bytes(const stg_domain *d, const stg_params *p, int64_t *by
     double b = 2 * r(19 * P * elem) + r(24 * ny * nz) + r(12 * ny * nz) + r(sizeof(StepCtl)) + r(24 * nx * ny) + r(48 * nx * ny) +
                r(8.0 * stg::step_grid_blocks(d->nx, d->ny, d->nz)) + 2 * r(16) + 2 * r(16) +
                r(8.0 * stg::mass_grid_blocks());
+    if (d->sponge_len > 0.0) b += r(4 * nx);
+    if (d->stats_every > 0) b += r(36.0 * nx * ny * std::ceil(nz / (double)stg::STAT_GROUP));
     if (d->bc_x == STG_BC_X_INLET_OUTLET) {
         double N = 1.0;
         if (p && p->n_modes > 0) N = p->n_modes;
         else if (p && p->alpha > 0.0) N = std::ceil(std::log(1.5 * std::max(ny, 2.0)) / std::log(1.0 + p->alpha) + 1.0);
-        if (d->sponge_len > 0.0) b += r(4 * nx);
         b += r(4 * N * ny) + r(4 * N * nz) + r(4 * N * ny) + r(12 * N) + 2 * r(8 * N) + r(24 * ny) + r(4 * ny) +
              r(48 * ny) + r(24 * ny) + r(16 * N);
     }

@@ -38,6 +38,7 @@ struct stg_lbm {
     float a_filter = 0.f;
     stg::StepCtl *ctl = nullptr;
     double *stat_mean = nullptr, *stat_rey = nullptr;
+    float *stat_part = nullptr;  // z-group sums of a sampling step (vector kernels)
     double *mass_partial = nullptr, *mass_out = nullptr;
     unsigned *mass_counter = nullptr;
     double *m_partial = nullptr, *m_out = nullptr;

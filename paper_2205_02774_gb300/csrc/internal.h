@@ -51,6 +51,8 @@ struct StepArgs {
     int stats_every, check_every;
     double *stat_mean;    // [3][ny][nx]
     double *stat_rey;     // [6][ny][nx]
+    float *stat_part;     // sampling steps of the vector kernels: FP32 sums per group of
+                          // STAT_GROUP z planes, [ceil(nz / STAT_GROUP)][9][ny][nx]
     double *mass_partial; // [gridDim.x * gridDim.y]
     unsigned *mass_counter;
     double *mass_out;     // [0]: last checked mass
@@ -116,6 +118,9 @@ cudaError_t launch_tma(const StepArgs &a, const void *tensor_map, int gx, int gy
 // Upper bound of the mass-partial slots of one step pass over every tile
 // that set_tile accepts (z chunks of at least MIN_ZC planes).
 constexpr int MIN_ZC = 4;
+// z planes per block on sampling steps of the vector kernels (fixed, so the
+// statistics do not depend on the launch tile)
+constexpr int STAT_GROUP = 32;
 int step_grid_blocks(int nx, int ny, int nz);
 int mass_grid_blocks();
 

@@ -480,10 +480,13 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
 
 // Sampling-step vector kernel over all x of rows 1..ny-2 (YEDGE false) or of
 // rows 0 and ny-1 (YEDGE true; that launch also advances the device step
-// counter).  The warps of a block are 8 z-lanes of one CPL*32-wide x chunk and
-// the block walks the whole z column, so the per-(x, y) statistics are summed
-// in shared memory without atomics and in a fixed order.  STATS is chosen on
-// the host (it knows the step count); plain steps use lbm_vec_zc_kernel.
+// counter).  Block (x chunk, row, group of STAT_GROUP z planes); its 8 warps
+// take every 8th plane of the group, so the block sums the group's velocity moments per
+// (x, y) in shared memory and writes them, in FP32, to the group's slot of
+// a.stat_part; stats_reduce_kernel then adds the groups in order in FP64.
+// The decomposition is fixed (no tile), so the statistics are deterministic
+// and independent of the launch tile.  STATS is chosen on the host (it knows
+// the step count); plain steps use lbm_vec_zc_kernel.
 template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP>
 __global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kernel(const StepArgs a)
 {
@@ -501,11 +504,14 @@ __global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kerne
 #pragma unroll
             for (int j = 0; j < CPL; ++j) sacc[wi][q][CPL * lane + j] = 0.f;
     }
-    const float sdr = vec_loop<S, REG, FORCE, STATS, YEDGE, SP>(a, sacc, x0, y, wi, a.nz, BZ);
+    static_assert(STAT_GROUP % BZ == 0, "whole planes per warp");
+    const int zb = STATS ? blockIdx.z * STAT_GROUP : 0;
+    const float sdr = vec_loop<S, REG, FORCE, STATS, YEDGE, SP>(a, sacc, x0, y, zb + wi, STATS ? min(zb + STAT_GROUP, a.nz) : a.nz, BZ);
     if (STATS) {
         __syncthreads();
         if (wi == 0) {
             const size_t m = (size_t)nx * ny;
+            float *part = a.stat_part + (size_t)blockIdx.z * 9 * m;
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
                 const int xc = x0 + CPL * lane + j;
@@ -513,17 +519,29 @@ __global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kerne
                 const size_t xy = (size_t)y * nx + xc;
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
-                    double sum = 0.0;
-                    for (int k = 0; k < BZ; ++k) sum += (double)sacc[k][q][CPL * lane + j];
-                    if (q < 3) a.stat_mean[q * m + xy] += sum;
-                    else a.stat_rey[(q - 3) * m + xy] += sum;
+                    float sum = 0.f;
+#pragma unroll
+                    for (int k = 0; k < BZ; ++k) sum += sacc[k][q][CPL * lane + j];
+                    part[q * m + xy] = sum;
                 }
             }
         }
     }
     if (do_check) mass_finish<BX * BZ>(a, sdr);
-    if (YEDGE && a.bump_t && blockIdx.x == 0 && blockIdx.y == 0 && lane == 0 && wi == 0)
+    if (YEDGE && a.bump_t && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && lane == 0 && wi == 0)
         a.ctl->t[a.parity ^ 1] = t + 1;
+}
+
+// Adds the z-group sums of a sampling step to the FP64 statistics, group by
+// group in index order (one thread per (x, y) and moment).
+__global__ void stats_reduce_kernel(const float *part, int groups, size_t m, double *stat_mean, double *stat_rey)
+{
+    const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;  // q * m + xy
+    if (k >= 9 * m) return;
+    double sum = 0.0;
+    for (int g = 0; g < groups; ++g) sum += (double)part[(size_t)g * 9 * m + k];
+    if (k < 3 * m) stat_mean[k] += sum;
+    else stat_rey[k - 3 * m] += sum;
 }
 
 // Plain-step vector kernel, tiled in z: block (x chunk, row, z chunk of
@@ -632,8 +650,9 @@ static Split split_of(const StepArgs &a, int cpl)
     return sp;
 }
 
+// Returns true when the pass left z-group statistics in a.stat_part.
 template <typename S, bool REG, bool FORCE, bool SP>
-static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *tmap, cudaStream_t s,
+static bool launch_forced(StepArgs a, const Split &sp, bool stats, const void *tmap, cudaStream_t s,
                           cudaStream_t side)
 {
     const dim3 block(BX, BZ);
@@ -643,9 +662,11 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
         const int nx = a.nx, ny = a.ny;
         const int rows_in = ny > 2 ? ny - 2 : 0, rows_edge = ny >= 2 ? 2 : 1;
         const int nz = a.nz;
-        // grids: sampling steps take whole z columns (statistics summed per
-        // block); plain steps take the tile's z chunks
-        dim3 gi(sp.nxv, rows_in), ge(sp.nxv, rows_edge);
+        // grids: sampling steps take fixed groups of STAT_GROUP planes (their
+        // sums go to a.stat_part and are reduced after the pass); plain steps
+        // take the tile's z chunks
+        const int groups = (nz + STAT_GROUP - 1) / STAT_GROUP;
+        dim3 gi(sp.nxv, rows_in, groups), ge(sp.nxv, rows_edge, groups);
         dim3 bi = block;
         if (!stats) {
             const int zc = a.tile_zc > 0 ? a.tile_zc : nz, wzc = a.tile_wall_zc > 0 ? a.tile_wall_zc : nz;
@@ -672,7 +693,7 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
         }
         if (stats) lbm_vec_kernel<S, REG, FORCE, true, true, SP><<<ge, block, 0, side>>>(ae);
         else lbm_vec_zc_kernel<S, REG, FORCE, 0, true, SP><<<ge, block, 0, side>>>(ae);
-        return;
+        return stats;
     }
     const bool tma = !SP && a.interior == 3 && tmap && sp.gx > 0 && sp.gy > 0 && (sp.ir - sp.il) % 2 == 0 &&
                      a.nx % 2 == 0 && 19.0 * a.nx * a.ny * a.nz < 4294967296.0 && tma_usable(a.nx, storage);
@@ -689,18 +710,19 @@ static void launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
         if (tma) launch_tma(ai, tmap, (sp.ir - sp.il) / 2, sp.gy, storage, REG ? 0 : 1, stats, s);
         else lbm_step_kernel<S, REG, FORCE, SP><<<dim3(sp.gx, sp.gy), block, 0, s>>>(ai);
     }
+    return false;
 }
 
 template <typename S, bool REG>
-static void launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaStream_t s, cudaStream_t side)
+static bool launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaStream_t s, cudaStream_t side)
 {
     const Split sp = split_of(a0, VecOf<S>::CPL);
     StepArgs a = a0;
     a.bump_t = 0;
     // the sponge is only compiled for unforced lattices (the host refuses a sponge with a force)
-    if (a.spf) launch_forced<S, REG, false, true>(a, sp, stats, tmap, s, side);
-    else if (a.has_force) launch_forced<S, REG, true, false>(a, sp, stats, tmap, s, side);
-    else launch_forced<S, REG, false, false>(a, sp, stats, tmap, s, side);
+    if (a.spf) return launch_forced<S, REG, false, true>(a, sp, stats, tmap, s, side);
+    if (a.has_force) return launch_forced<S, REG, true, false>(a, sp, stats, tmap, s, side);
+    return launch_forced<S, REG, false, false>(a, sp, stats, tmap, s, side);
 }
 
 // One fused step pass.  With a side stream and two events the edge work runs
@@ -720,17 +742,25 @@ cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stat
     // the inlet kernel writes the plane of the next step, which nothing in
     // this pass reads, so it runs on the branch beside the interior
     if (inlet && (e = launch_inlet(*inlet, es)) != cudaSuccess) return e;
+    bool reduce = false;
     if (storage == 0) {
-        if (collision == 0) launch_typed<float, true>(a, stats, tmap, s, es);
-        else launch_typed<float, false>(a, stats, tmap, s, es);
+        if (collision == 0) reduce = launch_typed<float, true>(a, stats, tmap, s, es);
+        else reduce = launch_typed<float, false>(a, stats, tmap, s, es);
     } else {
-        if (collision == 0) launch_typed<__half, true>(a, stats, tmap, s, es);
-        else launch_typed<__half, false>(a, stats, tmap, s, es);
+        if (collision == 0) reduce = launch_typed<__half, true>(a, stats, tmap, s, es);
+        else reduce = launch_typed<__half, false>(a, stats, tmap, s, es);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (forked) {
         if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(s, join, 0)) != cudaSuccess) return e;
+    }
+    if (reduce) {
+        const size_t m = (size_t)a.nx * a.ny;
+        const int groups = (a.nz + STAT_GROUP - 1) / STAT_GROUP;
+        const unsigned blocks = (unsigned)((9 * m + 255) / 256);
+        stats_reduce_kernel<<<blocks, 256, 0, s>>>(a.stat_part, groups, m, a.stat_mean, a.stat_rey);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
