@@ -1,9 +1,10 @@
 """Sponge zone of eq. (sponge_visco) on the GPU against the oracle.
 
 The zone scales the relaxation of the last sponge_len columns before the
-outlet; the tests cover the vector kernels (even nx, every tile), the scalar
-kernels (odd nx), the boundary-column kernel (the outlet column is inside
-the zone) and a periodic-x lattice with the zone over part of x."""
+outlet; the tests cover the vector kernels (even nx, every tile; the outlet
+node, rebuilt in the vector kernel, lies inside the zone), the scalar kernels
+(odd nx) and a periodic-x lattice with the zone over part of x.
+"""
 import numpy as np
 import pytest
 
