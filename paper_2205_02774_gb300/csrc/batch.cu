@@ -120,6 +120,7 @@ int order_members_after(stg_batch *b)
 // Block graph of B steps from the members' current step counters.
 int capture_block(stg_batch *b)
 {
+    const Range range("batch capture");
     drop_graph(b);
     cudaGraph_t g = nullptr;
     BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -158,6 +159,7 @@ constexpr int STABLE_BLOCKS = 3;
 // Graph of B steps of member d alone, on its branch stream.
 int capture_member(stg_batch *b, size_t d)
 {
+    const Range range("member capture");
     stg_lbm *h = b->m[d];
     if (b->mg[d]) cudaGraphExecDestroy(b->mg[d]);
     b->mg[d] = nullptr;
@@ -343,6 +345,7 @@ int stg_batch_block_steps(const stg_batch *b) { return b ? b->B : 0; }
 
 int stg_batch_step(stg_batch *b, int64_t n)
 {
+    const Range range("stg_batch_step");
     if (!b) return bfail(nullptr, STG_ERR_INVALID, "batch is NULL");
     if (n < 0) return bfail(b, STG_ERR_INVALID, "negative step count");
     for (size_t d = 0; d < b->m.size(); ++d) {
@@ -402,6 +405,7 @@ int stg_batch_sync(stg_batch *b)
 
 int stg_batch_autotune(stg_batch *b, int32_t trial_passes, stg_tile *chosen)
 {
+    const Range range("stg_batch_autotune");
     if (!b) return bfail(nullptr, STG_ERR_INVALID, "batch is NULL");
     if (b->m.empty()) return bfail(b, STG_ERR_INVALID, "empty batch");
     if (trial_passes < 1 || trial_passes > 1000) return bfail(b, STG_ERR_INVALID, "trial_passes must be in [1, 1000]");

@@ -643,6 +643,7 @@ extern "C" {
 int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const stg_params *stgp, uint64_t seed,
                    const stg_allocator *alloc, void *stream, stg_lbm **out)
 {
+    const Range range("stg_lbm_create");
     if (!out) return fail(nullptr, STG_ERR_INVALID, "out is NULL");
     *out = nullptr;
     int rc = validate(domain, rans, stgp);
@@ -799,6 +800,7 @@ int stg_lbm_estimate_bytes(const stg_domain *d, const stg_params *p, int64_t *by
 
 int stg_lbm_step(stg_lbm *h, int64_t n)
 {
+    const Range range("stg_lbm_step");
     if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
     if (h->batch) return fail(h, STG_ERR_INVALID, "the lattice is in a batch; step the batch");
     if (n < 0) return fail(h, STG_ERR_INVALID, "negative step count");
@@ -868,6 +870,7 @@ int stg_lbm_step_timed(stg_lbm *h, int64_t n, double *ms_step, double *ms_inlet)
 
 int stg_lbm_stats(stg_lbm *h, stg_stats *out)
 {
+    const Range range("stg_lbm_stats");
     if (!h || !out) return fail(h, STG_ERR_INVALID, "NULL argument");
     int rc = wait_stream(h);
     if (rc) return rc;
@@ -957,6 +960,7 @@ int stg_lbm_checkpoint_bytes(const stg_lbm *h, size_t *bytes)
 
 int stg_lbm_save(stg_lbm *h, void *host, size_t bytes)
 {
+    const Range range("stg_lbm_save");
     if (!h || !host) return fail(h, STG_ERR_INVALID, "NULL argument");
     if (bytes != ckpt_bytes(h)) return fail(h, STG_ERR_INVALID, "checkpoint size mismatch");
     int rc = wait_stream(h);
@@ -994,6 +998,7 @@ int stg_lbm_save(stg_lbm *h, void *host, size_t bytes)
 
 int stg_lbm_load(stg_lbm *h, const void *host, size_t bytes)
 {
+    const Range range("stg_lbm_load");
     if (!h || !host) return fail(h, STG_ERR_INVALID, "NULL argument");
     if (h->batch) return fail(h, STG_ERR_INVALID, "the lattice is in a batch; remove it first");
     if (bytes != ckpt_bytes(h)) return fail(h, STG_ERR_INVALID, "checkpoint size mismatch");
@@ -1190,6 +1195,7 @@ extern "C" {
 
 int stg_lbm_autotune(stg_lbm *h, int32_t trial_passes, stg_tile *chosen)
 {
+    const Range range("stg_lbm_autotune");
     if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
     if (h->batch) return fail(h, STG_ERR_INVALID, "the lattice is in a batch; tune the batch");
     if (trial_passes < 1 || trial_passes > 1000) return fail(h, STG_ERR_INVALID, "trial_passes must be in [1, 1000]");

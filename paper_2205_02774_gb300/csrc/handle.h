@@ -8,6 +8,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "internal.h"
 #include "stg_lbm.h"
@@ -68,6 +69,15 @@ struct stg_lbm {
 
 namespace stg {
 namespace host {
+
+// NVTX range for the host side of an entry point (visible in a profiler's
+// timeline; inert without one).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 int fail(stg_lbm *h, int code, const std::string &msg);
 int cuda_fail(stg_lbm *h, cudaError_t e, const char *what);

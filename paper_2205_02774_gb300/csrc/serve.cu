@@ -78,6 +78,7 @@ const char *stg_serve_last_error(void) { return g_serve_error.c_str(); }
 int stg_serve_run(const stg_job *jobs, int32_t n_jobs, const stg_serve_config *cfg, void *stream,
                   stg_job_result *results, stg_serve_report *report)
 {
+    const Range range("stg_serve_run");
     if (n_jobs < 0 || (n_jobs > 0 && (!jobs || !results)) || !cfg || !(cfg->hbm_budget_bytes > 0.0))
         return sfail(STG_ERR_INVALID, "serve: bad arguments");
     for (int32_t i = 0; i < n_jobs; ++i)
