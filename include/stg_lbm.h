@@ -62,7 +62,9 @@ extern "C" {
 #define STG_REGULARIZED 0   /* BGK relaxation of the regularized non-equilibrium part */
 #define STG_BGK 1           /* plain BGK, eq. (lbe) */
 /* stg_domain.bc_x */
-#define STG_BC_X_INLET_OUTLET 0 /* STG inlet at x = 0, pressure outlet at x = nx-1 */
+/* STG inlet at x = 0 (regularized Zou-He reconstruction of the inlet plane's velocity); pressure
+ * outlet at x = nx-1 (rho = 1, velocity of the neighbour x = nx-2 at the same step, regularized) */
+#define STG_BC_X_INLET_OUTLET 0
 #define STG_BC_X_PERIODIC 1
 /* stg_domain.bc_y */
 #define STG_BC_Y_WALLS 0    /* half-way bounce-back at y = -1/2 and y = ny - 1/2 */
