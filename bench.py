@@ -44,10 +44,15 @@ def _peaks():
 
 
 def _kernel_hash():
+    """Hash of the step kernels' source with comments and white space removed
+    (a comment edit does not change the kernel whose counters were taken)."""
     h = hashlib.sha256()
     for f in ("step_kernel.cu", "d3q19.cuh", "internal.h", "lbm_cell.cuh", "reduce.cuh"):
-        with open(os.path.join(ROOT, "paper_2205_02774_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2205_02774_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -675,7 +675,7 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
         }
         h->own_stream = true;
     }
-    int lo_prio = 0, hi_prio = 0;  // the edge branch gets the highest priority: its blocks start first
+    int lo_prio = 0, hi_prio = 0;  // the branch (wall rows, inlet plane) gets the highest priority: its blocks start first
     if (cudaEventCreateWithFlags(&h->ev_check, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||

@@ -11,9 +11,11 @@
 // bodyforce) and store.  On sampling steps the same pass accumulates the FP64
 // velocity statistics and the FP64 mass.
 //
-// Layout: SoA f[i][z][y][x].  A block is 32 consecutive x (one warp row) by 8
-// z-lanes at one y; each thread walks z with stride 8, so a block owns all z
-// of its (x, y) column and the statistics need no atomics.
+// Layout: SoA f[i][z][y][x].  The even-nx path (vector kernels) gives each
+// lane two consecutive x cells; plain steps cut the lattice into blocks of
+// (x chunk, row, z chunk) chosen by the launch tile, sampling steps into
+// fixed groups of z planes whose per-(x, y) sums are added in order.  The
+// odd-nx path (one cell per thread) keeps a block per (x chunk, row) column.
 #include <cuda_fp16.h>
 
 #include "d3q19.cuh"
@@ -725,9 +727,10 @@ static bool launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaS
     return launch_forced<S, REG, false, false>(a, sp, stats, tmap, s, side);
 }
 
-// One fused step pass.  With a side stream and two events the edge work runs
-// on a forked branch concurrently with the interior (both read only the
-// previous lattice and write disjoint cells); `s` waits for both.  `inlet`
+// One fused step pass.  With a side stream and two events the wall rows (or
+// the edge kernel on the scalar path) run on a forked branch concurrently
+// with the interior (both read only the previous lattice and write disjoint
+// cells); `s` waits for both.  `inlet`
 // (may be NULL) computes the next step's inlet plane on the branch.
 cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, const void *tmap,
                         cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, const InletArgs *inlet)
