@@ -154,3 +154,19 @@ def test_serve_memory_budget():
     assert [r["status"] for r in results[:4]] == [0, 0, 0, 0]
     assert results[4]["status"] == A.STG_ERR_NOMEM
     assert rep["completed"] == 4 and rep["failed"] == 1
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(storage="fp16s"), dict(stats_every=0), dict(bc_x="periodic"),
+                                dict(sponge_len=10.0), dict(n_modes=0)])
+def test_admission_estimate_bounds_the_allocation(kw):
+    """The serving loop admits jobs by stg_lbm_estimate_bytes; it must not
+    undercount what create() really allocates."""
+    from paper_2205_02774_gb300 import capi as A
+    from paper_2205_02774_gb300.channel import Channel, case_kwargs, create_structs
+    c = SMALL.with_(nx=96, ny=20, nz=18, **kw)
+    d, _, p, _ = create_structs(c.nx, c.ny, c.nz, **case_kwargs(c))
+    est = A.stg_lbm_estimate_bytes(d, p)
+    g = Channel.from_case(c)
+    used = g.info()["device_bytes"]
+    g.close()
+    assert used <= est <= 1.5 * used + 4e6
