@@ -215,6 +215,33 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def fp16_companion(c, args):
+    """The same channel with populations stored as shifted FP16, timed the
+    same way (autotuned tile, W warm-up steps, K steps between CUDA events),
+    so one bench line carries the FP16-storage vs FP32 comparison."""
+    import torch
+    from paper_2205_02774_gb300.channel import Channel
+    c16 = c.with_(storage="fp16s")
+    ch = Channel.from_case(c16, check_every=100, mass_tol=0.5)
+    tile = ch.autotune(20)
+    ch.step(args.warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(ch.stream)
+    ch.step(args.steps)
+    e1.record(ch.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    rc = ch.stats()["rc"]
+    ch.close()
+    peak, _ = _peaks()
+    bpc = BYTES_PER_CELL["fp16s"]
+    return {"storage": "fp16s", "value": c16.cells * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+            "ms_per_step": ms / args.steps, "hbm_frac_of_step": bpc * c16.cells * args.steps / (ms * 1e-3) / 1e9 / peak,
+            "tile": list(tile), "rc": rc}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -318,6 +345,8 @@ def run_ours(args):
         "gpu_launches": _launches_per_step(c) * args.steps,
         "clocks": clocks,
     }
+    if args.storage == "fp32" and not args.no_companion:
+        line["fp16s_companion"] = fp16_companion(c, args)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.storage, args.cpu_steps)
         line["cpu_baseline"].pop("seconds", None)
@@ -420,6 +449,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="", help="launch tile 'layout,zc,wall_zc' instead of the autotuner's")
+    ap.add_argument("--no-companion", action="store_true", help="skip the FP16-storage companion run")
     ap.add_argument("--members", type=int, default=64, help="ensemble workload: channels in the batch")
     ap.add_argument("--jobs", type=int, default=60, help="serve workload: jobs in the stream")
     ap.add_argument("--steps-scale", type=float, default=0.1, help="serve workload: scale of the step counts")
