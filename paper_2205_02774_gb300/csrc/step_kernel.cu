@@ -231,6 +231,7 @@ struct Vec<float, 2> {
         if (j) v.y = f;
         else v.x = f;
     }
+    static __device__ __forceinline__ raw pack(float lo, float hi) { return make_float2(lo, hi); }
     static __device__ __forceinline__ void st(float *p, raw v) { __stcs(reinterpret_cast<float2 *>(p), v); }
     static __device__ __forceinline__ void st1(float *p, raw v, int j) { __stcs(p + j, cell(v, j)); }
     // (x-1, x) from the left lane's (x-2, x-1) and ours (x, x+1); xl = x-1 when read directly
@@ -312,6 +313,15 @@ struct Vec<__half, 2> {
     {
         if (j) asm("{.reg .b16 lo, hi, n; mov.b32 {lo, hi}, %0; cvt.rn.f16.f32 n, %1; mov.b32 %0, {lo, n};}" : "+r"(v) : "f"(f));
         else asm("{.reg .b16 lo, hi, n; mov.b32 {lo, hi}, %0; cvt.rn.f16.f32 n, %1; mov.b32 %0, {n, hi};}" : "+r"(v) : "f"(f));
+    }
+    // both cells of the pair in one conversion (round to nearest even, as
+    // the one-value form): the first cell's results wait in FP32 registers,
+    // which the pair's inputs free as the second cell reads them
+    static __device__ __forceinline__ raw pack(float lo, float hi)
+    {
+        unsigned v;
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(v) : "f"(hi), "f"(lo));
+        return v;
     }
     static __device__ __forceinline__ void st(__half *p, raw v) { __stcs(reinterpret_cast<unsigned *>(p), v); }
     static __device__ __forceinline__ void st1(__half *p, raw v, int j)
@@ -430,6 +440,7 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
             else v[i] = V::shift_right(cur, sbase + (rbase + xr), side_r && !(inout && x + CPL == nx));
         }
         float upx = 0.f, upy = 0.f, upz = 0.f;  // velocity of the lane's previous cell
+        float gp[CPL == 2 ? Q : 1];             // first cell's results (pairs)
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
             float g[Q];
@@ -460,8 +471,16 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
             upx = ux;
             upy = uy;
             upz = uz;
+            if constexpr (CPL == 2) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) V::put(v[i], j, g[i]);
+                for (int i = 0; i < Q; ++i) {
+                    if (j == 0) gp[i] = g[i];
+                    else v[i] = V::pack(gp[i], g[i]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) V::put(v[i], j, g[i]);
+            }
             const bool counted = active;
             if (STATS && counted) {
                 float *sp = &sacc[wi][0][CPL * lane + j];
