@@ -328,6 +328,24 @@ struct Vec<__half, 2> {
     {
         __stcs(p + j, __ushort_as_half((unsigned short)(j ? v >> 16 : v & 0xffffu)));
     }
+    // (x-1, x) and (x+1, x+2) with the missing value read as one binary16 at
+    // a fixed offset from the pair's own address (row = element x): no
+    // shuffle, no separate halo address; valid wherever row[-1] and row[2]
+    // lie inside the allocation (the caller ensures it)
+    static __device__ __forceinline__ raw halo_left(raw cur, const __half *row)
+    {
+        const unsigned short h = __half_as_ushort(__ldg(row - 1));
+        raw v;
+        asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %1; mov.b32 %0, {%2, lo};}" : "=r"(v) : "r"(cur), "h"(h));
+        return v;
+    }
+    static __device__ __forceinline__ raw halo_right(raw cur, const __half *row)
+    {
+        const unsigned short h = __half_as_ushort(__ldg(row + 2));
+        raw v;
+        asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %1; mov.b32 %0, {hi, %2};}" : "=r"(v) : "r"(cur), "h"(h));
+        return v;
+    }
     // (x-1, x)
     static __device__ __forceinline__ raw shift_left(raw cur, const __half *xl, bool side)
     {
@@ -361,8 +379,15 @@ struct VecOf {
 // pressure outlet, whose velocity is that of the same lane's previous cell
 // x = nx-2; their pulled values from outside the lattice are never read.
 // STATS adds the per-cell velocity sums to the block's shared-memory slots.
+// H16 (binary16 pairs, inlet/outlet in x only): the x-shifted pairs take
+// their missing value by a 2-byte load beside the pair instead of a warp
+// shuffle.  Lane 0 of the first chunk then reads the element before its row
+// and the last lane the element after it; both lie inside the 19-plane
+// allocation (they are used only for c_x > 0 at x = 0, planes 1..13, and
+// c_x < 0 at x = nx-1, planes 2..14) and are the unknowns that the inlet and
+// outlet rebuilds replace.
 // Returns the thread's sum of rho - 1.
-template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP>
+template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP, bool H16 = false>
 __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX * VecOf<S>::CPL], int x0, int y,
                                           int zb, int ze, int zs)
 {
@@ -436,6 +461,11 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
             if (active) cur = V::ld(row);
             else cur = raw{};
             if (cx == 0) v[i] = cur;
+            else if constexpr (H16) {
+                if (!active) v[i] = raw{};
+                else if (cx > 0) v[i] = V::halo_left(cur, row);
+                else v[i] = V::halo_right(cur, row);
+            }
             else if (cx > 0) v[i] = V::shift_left(cur, sbase + (rbase + xl), side_l && !(inout && x == 0));
             else v[i] = V::shift_right(cur, sbase + (rbase + xr), side_r && !(inout && x + CPL == nx));
         }
@@ -579,7 +609,7 @@ struct ZcShape {
     static constexpr int MINB = (LEAN ? 32 : 24) / NW;  // resident blocks per SM
 };
 
-template <typename S, bool REG, bool FORCE, int LAYOUT, bool YEDGE, bool SP>
+template <typename S, bool REG, bool FORCE, int LAYOUT, bool YEDGE, bool SP, bool H16 = false>
 __global__ void __launch_bounds__(BX *ZcShape<LAYOUT, REG && !FORCE && !YEDGE>::NW,
                                   ZcShape<LAYOUT, REG && !FORCE && !YEDGE>::MINB)
     lbm_vec_zc_kernel(const StepArgs a)
@@ -595,9 +625,9 @@ __global__ void __launch_bounds__(BX *ZcShape<LAYOUT, REG && !FORCE && !YEDGE>::
     const bool do_check = a.check_every > 0 && ((t + 1) % a.check_every) == 0;
     float sdr;
     if (LAYOUT == 0)
-        sdr = vec_loop<S, REG, FORCE, false, YEDGE, SP>(a, nullptr, BX * CPL * blockIdx.x, y, zb + wi, ze, NW);
+        sdr = vec_loop<S, REG, FORCE, false, YEDGE, SP, H16>(a, nullptr, BX * CPL * blockIdx.x, y, zb + wi, ze, NW);
     else
-        sdr = vec_loop<S, REG, FORCE, false, YEDGE, SP>(a, nullptr, BX * CPL * (NW * blockIdx.x + wi), y, zb, ze, 1);
+        sdr = vec_loop<S, REG, FORCE, false, YEDGE, SP, H16>(a, nullptr, BX * CPL * (NW * blockIdx.x + wi), y, zb, ze, 1);
     if (do_check) mass_finish<BX * NW>(a, sdr);
     if (YEDGE && a.bump_t && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && wi == 0)
         a.ctl->t[a.parity ^ 1] = t + 1;
@@ -702,6 +732,8 @@ static bool launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
         }
         const int n_in = rows_in > 0 ? (int)(gi.x * gi.y * gi.z) : 0;
         const int n_edge = (int)(ge.x * ge.y * ge.z);
+        // binary16 pairs in an inlet/outlet lattice: x halo by 2-byte loads
+        const bool h16 = sizeof(S) == 2 && a.bc_x == 0;
         a.total_blocks = (unsigned)(n_in + n_edge);
         StepArgs ai = a, ae = a;
         ai.slot_base = 0;
@@ -709,10 +741,13 @@ static bool launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
         ae.bump_t = 1;
         if (n_in > 0) {
             if (stats) lbm_vec_kernel<S, REG, FORCE, true, false, SP><<<gi, block, 0, s>>>(ai);
+            else if (h16 && a.tile_layout == 1) lbm_vec_zc_kernel<S, REG, FORCE, 1, false, SP, sizeof(S) == 2><<<gi, bi, 0, s>>>(ai);
+            else if (h16) lbm_vec_zc_kernel<S, REG, FORCE, 0, false, SP, sizeof(S) == 2><<<gi, bi, 0, s>>>(ai);
             else if (a.tile_layout == 1) lbm_vec_zc_kernel<S, REG, FORCE, 1, false, SP><<<gi, bi, 0, s>>>(ai);
             else lbm_vec_zc_kernel<S, REG, FORCE, 0, false, SP><<<gi, bi, 0, s>>>(ai);
         }
         if (stats) lbm_vec_kernel<S, REG, FORCE, true, true, SP><<<ge, block, 0, side>>>(ae);
+        else if (h16) lbm_vec_zc_kernel<S, REG, FORCE, 0, true, SP, sizeof(S) == 2><<<ge, block, 0, side>>>(ae);
         else lbm_vec_zc_kernel<S, REG, FORCE, 0, true, SP><<<ge, block, 0, side>>>(ae);
         return stats;
     }
