@@ -436,6 +436,10 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
         unsigned Pv, nxv;
         asm volatile("mov.u32 %0, %1;" : "=r"(Pv) : "r"(a.P));
         asm volatile("mov.u32 %0, %1;" : "=r"(nxv) : "r"((unsigned)nx));
+        // plane stride in bytes (opaque too): a population's address is one
+        // wide multiply-add i * Pb on its row's byte pointer
+        unsigned Pb;
+        asm volatile("mov.u32 %0, %1;" : "=r"(Pb) : "r"(a.P * (unsigned)sizeof(S)));
         const unsigned row0 = ((unsigned)z * ny + y) * nx;
         const unsigned here = row0 + x;
         const unsigned dzm = (z == 0) ? -(nz - 1) * nxy : nxy;
@@ -456,7 +460,8 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
             const unsigned dz = cz > 0 ? dzm : (cz < 0 ? dzp : 0u);
             const unsigned dy = cy > 0 ? (YEDGE ? (unsigned)ym_off : nxv) : (cy < 0 ? (YEDGE ? (unsigned)yp_off : 0u - nxv) : 0u);
             const unsigned rbase = i * Pv + row0 - dz - dy;  // plane i, row (y - c_y, z - c_z)
-            const S *row = sbase + (rbase + x);
+            const unsigned rofs = row0 - dz - dy + x;         // element x of that row in plane 0
+            const S *row = reinterpret_cast<const S *>(reinterpret_cast<const char *>(sbase + rofs) + (size_t)i * Pb);
             raw cur;
             if (active) cur = V::ld(row);
             else cur = raw{};
@@ -523,7 +528,8 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
         }
         if (active) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) V::st(dbase + (i * Pv + here), v[i]);
+            for (int i = 0; i < Q; ++i)
+                V::st(reinterpret_cast<S *>(reinterpret_cast<char *>(dbase + here) + (size_t)i * Pb), v[i]);
         }
     }
     return sdr;
