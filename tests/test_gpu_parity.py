@@ -152,10 +152,15 @@ def test_poiseuille_gpu(collision, lam):
     assert normwise(ux, exact) < 2e-4
 
 
-@pytest.mark.parametrize("dims", [(64, 32, 32), (200, 6, 5), (101, 5, 7), (260, 5, 4)])
-def test_fp16_single_step(dims):
+@pytest.mark.parametrize("dims,kw", [
+    ((64, 32, 32), dict()), ((200, 6, 5), dict()), ((101, 5, 7), dict()),
+    ((260, 5, 4), dict()),                                            # ragged last chunk, 2-byte x halo
+    ((130, 6, 5), dict(bc_x="periodic", force=(2e-5, 0.0, 1e-5))),    # periodic x: shuffled x halo
+    ((64, 8, 4), dict(bc_x="periodic", bc_y="periodic", collision="bgk")),
+])
+def test_fp16_single_step(dims, kw):
     nx, ny, nz = dims
-    c = SMALL.with_(storage="fp16s", stats_every=0, nx=nx, ny=ny, nz=nz)
+    c = SMALL.with_(storage="fp16s", stats_every=0, nx=nx, ny=ny, nz=nz, **kw)
     gpu, orc = pair(c)
     f = perturbed_equilibrium_field(c.nx, c.ny, c.nz, seed=4)
     bits = fp16_bits(f)
