@@ -166,8 +166,29 @@ def aggregate_ranks(ms_local, cells_per_rank, steps, dist=None, device="cpu"):
     return ms, cells * steps / (ms * 1e-3) / 1e6
 
 
+def _oracle_single_thread(workload, storage, ny=16, steps=1):
+    """The oracle on one host thread (a child process with OMP_NUM_THREADS=1):
+    `steps` steps of an nx x ny x nz slice of the workload (full streamwise
+    length and span, fewer wall-normal rows)."""
+    code = ("import sys, time, json; sys.path.insert(0, %r); import oracle; from workloads import case; "
+            "c = case(%r).with_(storage=%r, ny=%d); s = oracle.Sim.from_case(c); t0 = time.perf_counter(); "
+            "s.step(%d); dt = time.perf_counter() - t0; "
+            "print(json.dumps({'value': c.cells * %d / dt / 1e6, 'threads': oracle.threads(), "
+            "'shape': [c.nx, c.ny, c.nz]}))") % (ROOT, workload, storage, ny, steps, steps)
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, OMP_NUM_THREADS="1"),
+                             capture_output=True, text=True, timeout=600)
+        d = json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, not fatal: the all-core figure stands
+        return {"error": str(e)[:200]}
+    nx, ny_, nz = d["shape"]
+    return {"value": d["value"], "unit": "MLUPS", "cores": d["threads"],
+            "sample": f"{steps} step of a {nx}x{ny_}x{nz} slice of the {workload} channel (FP64, one thread)"}
+
+
 def cpu_baseline(workload, storage, steps):
-    """The CPU FP64 oracle, as it stands, on a bounded sample of the workload."""
+    """The CPU FP64 oracle, as it stands, on a bounded sample of the workload:
+    all host cores (OpenMP over z), plus the same oracle on one thread."""
     import oracle
     from workloads import case
     c = case(workload).with_(storage=storage)
@@ -177,7 +198,8 @@ def cpu_baseline(workload, storage, steps):
     dt = time.perf_counter() - t0
     del sim
     return {"value": c.cells * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{steps} full steps of the {workload} lattice (FP64, OpenMP over z)", "seconds": dt}
+            "sample": f"{steps} full steps of the {workload} lattice (FP64, OpenMP over z)", "seconds": dt,
+            "single_thread": _oracle_single_thread(workload, storage)}
 
 
 def run_reference(args):
