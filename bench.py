@@ -81,6 +81,16 @@ def _launches_per_step(c):
     return inlet + 2
 
 
+def _launches(c, t0, steps):
+    """Kernels the steps t0 .. t0+steps-1 enqueue: _launches_per_step each, plus
+    the statistics reduction after every sampling step ((t + 1) % stats_every
+    == 0) of the vector path."""
+    n = _launches_per_step(c) * steps
+    if c.stats_every > 0 and c.nx % 2 == 0 and c.nx >= 4:
+        n += sum(1 for t in range(t0, t0 + steps) if (t + 1) % c.stats_every == 0)
+    return n
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -364,7 +374,7 @@ def run_ours(args):
                      "inlet_kernel_ms": ms_inlet},
         "hbm_frac_of_step": bpc * c.cells * args.steps / (ms * 1e-3) / 1e9 / peak,
         "e2e": e2e,
-        "gpu_launches": _launches_per_step(c) * args.steps,
+        "gpu_launches": _launches(c, args.warmup, args.steps),
         "clocks": clocks,
     }
     if args.storage == "fp32" and not args.no_companion:
@@ -424,7 +434,8 @@ def run_ensemble(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "scope": "whole step incl. inlet kernels",
                          "peak_source": f"{peak_kind} hbm_gbs (copy)"},
-            "failed_members": bad, "clocks": clocks}
+            "failed_members": bad, "clocks": clocks,
+            "gpu_launches": sum(_launches(j.case, args.warmup, args.steps) for j in jobs)}
     b.close()
     for ch in chans:
         ch.close()
