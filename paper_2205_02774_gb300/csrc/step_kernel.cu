@@ -542,10 +542,12 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
 // (x, y) in shared memory and writes them, in FP32, to the group's slot of
 // a.stat_part; stats_reduce_kernel then adds the groups in order in FP64.
 // The decomposition is fixed (no tile), so the statistics are deterministic
-// and independent of the launch tile.  STATS is chosen on the host (it knows
+// and independent of the launch tile.  H16 as in vec_loop; the binary16
+// regularized unforced interior instance fits 64 registers (32 warps per SM).  STATS is chosen on the host (it knows
 // the step count); plain steps use lbm_vec_zc_kernel.
-template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP>
-__global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kernel(const StepArgs a)
+template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP, bool H16 = false>
+__global__ void __launch_bounds__(BX *BZ, (REG && (!STATS || (H16 && !FORCE && !YEDGE))) ? 4 : 3)
+    lbm_vec_kernel(const StepArgs a)
 {
     constexpr int CPL = VecOf<S>::CPL;
     __shared__ float sacc[STATS ? BZ : 1][9][BX * CPL];  // per-thread statistics slots
@@ -563,7 +565,7 @@ __global__ void __launch_bounds__(BX *BZ, (REG && !STATS) ? 4 : 3) lbm_vec_kerne
     }
     static_assert(STAT_GROUP % BZ == 0, "whole planes per warp");
     const int zb = STATS ? blockIdx.z * STAT_GROUP : 0;
-    const float sdr = vec_loop<S, REG, FORCE, STATS, YEDGE, SP>(a, sacc, x0, y, zb + wi, STATS ? min(zb + STAT_GROUP, a.nz) : a.nz, BZ);
+    const float sdr = vec_loop<S, REG, FORCE, STATS, YEDGE, SP, H16>(a, sacc, x0, y, zb + wi, STATS ? min(zb + STAT_GROUP, a.nz) : a.nz, BZ);
     if (STATS) {
         __syncthreads();
         if (wi == 0) {
@@ -746,13 +748,15 @@ static bool launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
         ae.slot_base = n_in;
         ae.bump_t = 1;
         if (n_in > 0) {
-            if (stats) lbm_vec_kernel<S, REG, FORCE, true, false, SP><<<gi, block, 0, s>>>(ai);
+            if (stats && h16) lbm_vec_kernel<S, REG, FORCE, true, false, SP, sizeof(S) == 2><<<gi, block, 0, s>>>(ai);
+            else if (stats) lbm_vec_kernel<S, REG, FORCE, true, false, SP><<<gi, block, 0, s>>>(ai);
             else if (h16 && a.tile_layout == 1) lbm_vec_zc_kernel<S, REG, FORCE, 1, false, SP, sizeof(S) == 2><<<gi, bi, 0, s>>>(ai);
             else if (h16) lbm_vec_zc_kernel<S, REG, FORCE, 0, false, SP, sizeof(S) == 2><<<gi, bi, 0, s>>>(ai);
             else if (a.tile_layout == 1) lbm_vec_zc_kernel<S, REG, FORCE, 1, false, SP><<<gi, bi, 0, s>>>(ai);
             else lbm_vec_zc_kernel<S, REG, FORCE, 0, false, SP><<<gi, bi, 0, s>>>(ai);
         }
-        if (stats) lbm_vec_kernel<S, REG, FORCE, true, true, SP><<<ge, block, 0, side>>>(ae);
+        if (stats && h16) lbm_vec_kernel<S, REG, FORCE, true, true, SP, sizeof(S) == 2><<<ge, block, 0, side>>>(ae);
+        else if (stats) lbm_vec_kernel<S, REG, FORCE, true, true, SP><<<ge, block, 0, side>>>(ae);
         else if (h16) lbm_vec_zc_kernel<S, REG, FORCE, 0, true, SP, sizeof(S) == 2><<<ge, block, 0, side>>>(ae);
         else lbm_vec_zc_kernel<S, REG, FORCE, 0, true, SP><<<ge, block, 0, side>>>(ae);
         return stats;
