@@ -51,3 +51,21 @@ def test_single_rank_aggregation():
     import bench
     ms, value = bench.aggregate_ranks(4.0, 2.0e6, 100)
     assert ms == 4.0 and value == pytest.approx(2.0e6 * 100 / 4e-3 / 1e6)
+
+
+def test_launch_count_includes_statistics_reductions():
+    """gpu_launches: per step the inlet kernel and the two step launches of the
+    vector path, plus one statistics reduction after every sampling step
+    ((t + 1) % stats_every == 0) in the timed range; the scalar path (odd nx)
+    launches the inlet, interior and edge kernels and no reduction."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from workloads import case
+    c = case("channel_768x128x192")
+    assert c.stats_every == 10
+    assert bench._launches_per_step(c) == 3
+    assert bench._launches(c, 200, 4000) == 3 * 4000 + 400
+    assert bench._launches(c, 5, 10) == 30 + 1            # t = 9 samples
+    assert bench._launches(c.with_(stats_every=0), 5, 10) == 30
+    odd = c.with_(nx=767)
+    assert bench._launches(odd, 0, 20) == 3 * 20
