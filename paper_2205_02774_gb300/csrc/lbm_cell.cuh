@@ -96,25 +96,25 @@ __device__ __forceinline__ void rebuild(float (&g)[Q], float drho, float ux, flo
 // whole update is a few dozen fused multiply-adds.
 // SP: sponge zone, eq. (sponge_visco): the cell's viscosity is nu_eff times
 // nuf, i.e. tau = 1/2 + nuf (tau_eff - 1/2).
+// collide_sd is the same from the pair sums s_p = g_a + g_b and differences
+// d_p = g_a - g_b of the 9 opposite pairs (a = 2p+1, b = 2p+2) and
+// drho0 = g_0 + s_0, which the caller may form without converting every
+// population; g then only carries the input of the BGK term K g_i and
+// receives the result.
 template <bool REG, bool FORCE, bool SP = false>
-__device__ __forceinline__ void collide(float (&g)[Q], float tau0, float kq, float Fx, float Fy, float Fz,
-                                        float &rho_o, float &ux_o, float &uy_o, float &uz_o, float nuf = 1.0f)
+__device__ __forceinline__ void collide_sd(float (&g)[Q], const float (&s)[9], const float (&d)[9], float drho0,
+                                           float tau0, float kq, float Fx, float Fy, float Fz, float &rho_o,
+                                           float &ux_o, float &uy_o, float &uz_o, float nuf = 1.0f)
 {
-    float s[9], d[9];
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-        s[p] = g[2 * p + 1] + g[2 * p + 2];
-        d[p] = g[2 * p + 1] - g[2 * p + 2];
-    }
     // moments, eqs. (density), (momentum), (tensor): rho = 1 + sum g,
     // rho u = sum c g (+ F/2), Pi = sum c c g + I/3
-    float drho = g[0], jx = 0.f, jy = 0.f, jz = 0.f;
+    float drho = drho0, jx = 0.f, jy = 0.f, jz = 0.f;
     float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
         const int i = 2 * p + 1;
         const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        drho += s[p];
+        if (p) drho += s[p];
         if (cx) jx += cx * d[p];
         if (cy) jy += cy * d[p];
         if (cz) jz += cz * d[p];
@@ -247,6 +247,20 @@ __device__ __forceinline__ void collide(float (&g)[Q], float tau0, float kq, flo
     ux_o = ux;
     uy_o = uy;
     uz_o = uz;
+}
+
+// collide: from the 19 shifted populations g of the cell
+template <bool REG, bool FORCE, bool SP = false>
+__device__ __forceinline__ void collide(float (&g)[Q], float tau0, float kq, float Fx, float Fy, float Fz,
+                                        float &rho_o, float &ux_o, float &uy_o, float &uz_o, float nuf = 1.0f)
+{
+    float s[9], d[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        s[p] = g[2 * p + 1] + g[2 * p + 2];
+        d[p] = g[2 * p + 1] - g[2 * p + 2];
+    }
+    collide_sd<REG, FORCE, SP>(g, s, d, g[0] + s[0], tau0, kq, Fx, Fy, Fz, rho_o, ux_o, uy_o, uz_o, nuf);
 }
 
 }  // namespace stg

@@ -309,6 +309,23 @@ struct Vec<__half, 2> {
         else asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %1; cvt.f32.f16 %0, lo;}" : "=f"(f) : "r"(v));
         return f;
     }
+    // h_j + c and h_j - c in FP32 with the binary16 half j of the pair as an
+    // operand (mixed-precision add/sub, sm_100 and later; the half converts
+    // exactly, so each equals the FP32 sum of the converted value)
+    static __device__ __forceinline__ float add_h(raw v, int j, float c)
+    {
+        float r;
+        if (j) asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %1; add.rn.f32.f16 %0, hi, %2;}" : "=f"(r) : "r"(v), "f"(c));
+        else asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %1; add.rn.f32.f16 %0, lo, %2;}" : "=f"(r) : "r"(v), "f"(c));
+        return r;
+    }
+    static __device__ __forceinline__ float sub_h(raw v, int j, float c)
+    {
+        float r;
+        if (j) asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %1; sub.rn.f32.f16 %0, hi, %2;}" : "=f"(r) : "r"(v), "f"(c));
+        else asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %1; sub.rn.f32.f16 %0, lo, %2;}" : "=f"(r) : "r"(v), "f"(c));
+        return r;
+    }
     static __device__ __forceinline__ void put(raw &v, int j, float f)
     {
         if (j) asm("{.reg .b16 lo, hi, n; mov.b32 {lo, hi}, %0; cvt.rn.f16.f32 n, %1; mov.b32 %0, {lo, n};}" : "+r"(v) : "f"(f));
@@ -394,6 +411,8 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
     constexpr int CPL = VecOf<S>::CPL;
     using V = Vec<S, CPL>;
     using raw = typename V::raw;
+    // binary16 pairs, regularized collision: pair sums by mixed-precision adds
+    constexpr bool MIXED = REG && sizeof(S) == 2 && CPL == 2;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int nxy = nx * ny;
     const int lane = threadIdx.x, wi = threadIdx.y;
@@ -479,30 +498,61 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
             float g[Q];
+            // boundary nodes of this cell (inlet x = 0 at j = 0, outlet x = nx-1 at the last j)
+            const bool node = (j == 0 && at_inlet) || (j == CPL - 1 && at_outlet);
+            auto rebuild_node = [&](float (&gg)[Q]) {
+                if (j == 0 && at_inlet) {
+                    // Zou-He density, eq. (density_bc): parallel set + 2 x leaving set,
+                    // rho_bc - 1 = (S_g + u_x)/(1 - u_x) in shifted variables; the
+                    // unknowns (c_x > 0, their sources lie outside) are not read
+                    const size_t pc = (size_t)z * ny + y, pl3 = (size_t)ny * nz;
+                    const float ubx = a.ubc[pc], uby = a.ubc[pl3 + pc], ubz = a.ubc[2 * pl3 + pc];
+                    float par = 0.f, lv = 0.f;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) g[i] = V::cell(v[i], j);
-            if (j == 0 && at_inlet) {
-                // Zou-He density, eq. (density_bc): parallel set + 2 x leaving set,
-                // rho_bc - 1 = (S_g + u_x)/(1 - u_x) in shifted variables; the
-                // unknowns (c_x > 0, their sources lie outside) are not read
-                const size_t pc = (size_t)z * ny + y, pl3 = (size_t)ny * nz;
-                const float ubx = a.ubc[pc], uby = a.ubc[pl3 + pc], ubz = a.ubc[2 * pl3 + pc];
-                float par = 0.f, lv = 0.f;
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    if (cx_of(i) == 0) par += g[i];
-                    if (cx_of(i) < 0) lv += g[i];
+                    for (int i = 0; i < Q; ++i) {
+                        if (cx_of(i) == 0) par += gg[i];
+                        if (cx_of(i) < 0) lv += gg[i];
+                    }
+                    rebuild<1>(gg, (par + 2.0f * lv + ubx) / (1.0f - ubx), ubx, uby, ubz);
                 }
-                rebuild<1>(g, (par + 2.0f * lv + ubx) / (1.0f - ubx), ubx, uby, ubz);
-            }
-            if (j == CPL - 1 && at_outlet) {
-                // zero-gradient pressure outlet: rho = 1 and the velocity of the
-                // neighbour x = nx-2 (this lane's previous cell) at this step
-                rebuild<-1>(g, 0.0f, upx, upy, upz);
-            }
+                if (j == CPL - 1 && at_outlet) {
+                    // zero-gradient pressure outlet: rho = 1 and the velocity of the
+                    // neighbour x = nx-2 (this lane's previous cell) at this step
+                    rebuild<-1>(gg, 0.0f, upx, upy, upz);
+                }
+            };
             float rho, ux, uy, uz;
-            collide<REG, FORCE, SP>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz,
-                                    SP && active ? __ldg(a.spf + x + j) : 1.0f);
+            const float nuf = SP && active ? __ldg(a.spf + x + j) : 1.0f;
+            if constexpr (MIXED) {
+                // regularized collision of binary16 pairs: only the pair sums and
+                // differences enter, formed with one conversion per pair
+                float s[9], d[9], drho0;
+                if (node) {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) g[i] = V::cell(v[i], j);
+                    rebuild_node(g);
+#pragma unroll
+                    for (int p = 0; p < 9; ++p) {
+                        s[p] = g[2 * p + 1] + g[2 * p + 2];
+                        d[p] = g[2 * p + 1] - g[2 * p + 2];
+                    }
+                    drho0 = g[0] + s[0];
+                } else {
+#pragma unroll
+                    for (int p = 0; p < 9; ++p) {
+                        const float b = V::cell(v[2 * p + 2], j);
+                        s[p] = V::add_h(v[2 * p + 1], j, b);
+                        d[p] = V::sub_h(v[2 * p + 1], j, b);
+                    }
+                    drho0 = V::add_h(v[0], j, s[0]);
+                }
+                collide_sd<REG, FORCE, SP>(g, s, d, drho0, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz, nuf);
+            } else {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) g[i] = V::cell(v[i], j);
+                if (node) rebuild_node(g);
+                collide<REG, FORCE, SP>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz, nuf);
+            }
             upx = ux;
             upy = uy;
             upz = uz;
