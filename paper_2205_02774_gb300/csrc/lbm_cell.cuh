@@ -91,7 +91,9 @@ __device__ __forceinline__ void rebuild(float (&g)[Q], float drho, float ux, flo
 //   BGK:         a0 = w (drho - 1.5 rho u.u) - 3 kf u.F
 //                B  = 3 w rho u + 3 kf F
 //                A  = 4.5 w rho u u + 9 kf sym(u F)
-// (w = 1/tau_eff here, kf = 1 - w/2).  The 18 moving populations come in
+// (w = 1/tau_eff here, kf = 1 - w/2).  Outputs: the density excess
+// drho = rho - 1 (the sum of the shifted populations, before rho is rounded)
+// and the velocity u.  The 18 moving populations come in
 // opposite pairs, and the edge pairs (a, b, +-) share A_aa + A_bb, so the
 // whole update is a few dozen fused multiply-adds.
 // SP: sponge zone, eq. (sponge_visco): the cell's viscosity is nu_eff times
@@ -103,7 +105,7 @@ __device__ __forceinline__ void rebuild(float (&g)[Q], float drho, float ux, flo
 // receives the result.
 template <bool REG, bool FORCE, bool SP = false>
 __device__ __forceinline__ void collide_sd(float (&g)[Q], const float (&s)[9], const float (&d)[9], float drho0,
-                                           float tau0, float kq, float Fx, float Fy, float Fz, float &rho_o,
+                                           float tau0, float kq, float Fx, float Fy, float Fz, float &drho_o,
                                            float &ux_o, float &uy_o, float &uz_o, float nuf = 1.0f)
 {
     // moments, eqs. (density), (momentum), (tensor): rho = 1 + sum g,
@@ -243,7 +245,7 @@ __device__ __forceinline__ void collide_sd(float (&g)[Q], const float (&s)[9], c
             g[17] = fmaf(K, g[17], e17 + o17); g[18] = fmaf(K, g[18], e17 - o17);
         }
     }
-    rho_o = rho;
+    drho_o = drho;
     ux_o = ux;
     uy_o = uy;
     uz_o = uz;
@@ -252,7 +254,7 @@ __device__ __forceinline__ void collide_sd(float (&g)[Q], const float (&s)[9], c
 // collide: from the 19 shifted populations g of the cell
 template <bool REG, bool FORCE, bool SP = false>
 __device__ __forceinline__ void collide(float (&g)[Q], float tau0, float kq, float Fx, float Fy, float Fz,
-                                        float &rho_o, float &ux_o, float &uy_o, float &uz_o, float nuf = 1.0f)
+                                        float &drho_o, float &ux_o, float &uy_o, float &uz_o, float nuf = 1.0f)
 {
     float s[9], d[9];
 #pragma unroll
@@ -260,7 +262,7 @@ __device__ __forceinline__ void collide(float (&g)[Q], float tau0, float kq, flo
         s[p] = g[2 * p + 1] + g[2 * p + 2];
         d[p] = g[2 * p + 1] - g[2 * p + 2];
     }
-    collide_sd<REG, FORCE, SP>(g, s, d, g[0] + s[0], tau0, kq, Fx, Fy, Fz, rho_o, ux_o, uy_o, uz_o, nuf);
+    collide_sd<REG, FORCE, SP>(g, s, d, g[0] + s[0], tau0, kq, Fx, Fy, Fz, drho_o, ux_o, uy_o, uz_o, nuf);
 }
 
 }  // namespace stg

@@ -168,8 +168,8 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
                     }
                 }
             }
-            float rho, ux, uy, uz;
-            collide<REG, FORCE, SP>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz, SP ? __ldg(a.spf + x) : 1.0f);
+            float drho, ux, uy, uz;
+            collide<REG, FORCE, SP>(g, tau0, kq, Fx, Fy, Fz, drho, ux, uy, uz, SP ? __ldg(a.spf + x) : 1.0f);
 #pragma unroll
             for (int i = 0; i < Q; ++i) Pop<S>::st(static_cast<S *>(a.dstp[i]) + here, g[i]);
             if (do_stats) {
@@ -177,7 +177,7 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
                 s00 += ux * ux; s11 += uy * uy; s22 += uz * uz;
                 s01 += ux * uy; s02 += ux * uz; s12 += uy * uz;
             }
-            if (do_check) sdr += rho - 1.0f;
+            if (do_check) sdr += drho;
         }
     }
 
@@ -521,7 +521,7 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
                     rebuild<-1>(gg, 0.0f, upx, upy, upz);
                 }
             };
-            float rho, ux, uy, uz;
+            float drho, ux, uy, uz;
             const float nuf = SP && active ? __ldg(a.spf + x + j) : 1.0f;
             if constexpr (MIXED) {
                 // regularized collision of binary16 pairs: only the pair sums and
@@ -546,12 +546,12 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
                     }
                     drho0 = V::add_h(v[0], j, s[0]);
                 }
-                collide_sd<REG, FORCE, SP>(g, s, d, drho0, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz, nuf);
+                collide_sd<REG, FORCE, SP>(g, s, d, drho0, tau0, kq, Fx, Fy, Fz, drho, ux, uy, uz, nuf);
             } else {
 #pragma unroll
                 for (int i = 0; i < Q; ++i) g[i] = V::cell(v[i], j);
                 if (node) rebuild_node(g);
-                collide<REG, FORCE, SP>(g, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz, nuf);
+                collide<REG, FORCE, SP>(g, tau0, kq, Fx, Fy, Fz, drho, ux, uy, uz, nuf);
             }
             upx = ux;
             upy = uy;
@@ -574,7 +574,7 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
                 sp[3 * L] += ux * ux; sp[4 * L] += uy * uy; sp[5 * L] += uz * uz;
                 sp[6 * L] += ux * uy; sp[7 * L] += ux * uz; sp[8 * L] += uy * uz;
             }
-            if (counted) sdr += rho - 1.0f;
+            if (counted) sdr += drho;
         }
         if (active) {
 #pragma unroll

@@ -254,8 +254,8 @@ __global__ void __launch_bounds__(32 * TW, 6) lbm_tma_kernel(const StepArgs a, c
                 float gg[Q];
 #pragma unroll
                 for (int i = 0; i < Q; ++i) gg[i] = half ? ST::hi(v[i]) : ST::lo(v[i]);
-                float rho, ux, uy, uz;
-                collide<REG, FORCE>(gg, tau0, kq, Fx, Fy, Fz, rho, ux, uy, uz);
+                float drho, ux, uy, uz;
+                collide<REG, FORCE>(gg, tau0, kq, Fx, Fy, Fz, drho, ux, uy, uz);
                 if (half == 0) {
 #pragma unroll
                     for (int i = 0; i < Q; ++i) v[i] = ST::put_lo(v[i], gg[i]);
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(32 * TW, 6) lbm_tma_kernel(const StepArgs a, c
                     sp[3 * 64] += ux * ux; sp[4 * 64] += uy * uy; sp[5 * 64] += uz * uz;
                     sp[6 * 64] += ux * uy; sp[7 * 64] += ux * uz; sp[8 * 64] += uy * uz;
                 }
-                sdr += rho - 1.0f;
+                sdr += drho;
             }
         }
     }
