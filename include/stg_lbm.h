@@ -171,10 +171,12 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
  * check saw NaN/Inf or mass drift, else STG_OK or STG_ERR_CUDA. */
 int stg_lbm_step(stg_lbm *h, int64_t n);
 
-/* Enqueue n steps as individual launches and report the mean device time of
- * one launch of each kernel, measured with CUDA events on the handle's stream
- * (ms_step: fused step kernel, ms_inlet: STG inlet kernel; either may be
- * NULL).  Synchronises the stream.  Same physics as stg_lbm_step. */
+/* Enqueue n steps as individual launches and report mean device times,
+ * measured with CUDA events on the handle's stream (ms_step: one step pass,
+ * i.e. the fused stream/collide launches of a step and, on sampling steps,
+ * the statistics reduction; ms_inlet: the STG inlet kernel; either pointer may
+ * be NULL).  Synchronises the stream.  Same physics as stg_lbm_step.
+ * Errors: those of stg_lbm_step and stg_lbm_stats. */
 int stg_lbm_step_timed(stg_lbm *h, int64_t n, double *ms_step, double *ms_inlet);
 
 /* Wait for the handle's stream (bounded by timeout_s seconds, polling) and
@@ -183,9 +185,12 @@ int stg_lbm_step_timed(stg_lbm *h, int64_t n, double *ms_step, double *ms_inlet)
 int stg_lbm_stats(stg_lbm *h, stg_stats *out);
 
 /* Copy the populations (storage format g_i = f_i - w_i, 19*nx*ny*nz elements
- * of 4 or 2 bytes)
- * to or from host memory.  set_state also sets the step counter to `step` and
- * restarts the temporal filter.  `bytes` must equal the state size. */
+ * of 4 or 2 bytes, layout f[i][z][y][x]) to or from host memory owned by the
+ * caller; both wait for the handle's stream.  set_state also sets the step
+ * counter to `step` (>= 0), restarts the temporal filter and takes the state's
+ * mass as the reference of the mass check.  `bytes` must equal the state
+ * size.  Errors: STG_ERR_INVALID (NULL, size mismatch, negative step, a
+ * lattice in a batch for set_state), STG_ERR_TIMEOUT, STG_ERR_CUDA. */
 int stg_lbm_get_state(stg_lbm *h, void *host, size_t bytes);
 int stg_lbm_set_state(stg_lbm *h, const void *host, size_t bytes, int64_t step);
 
@@ -207,13 +212,19 @@ int stg_lbm_get_block(stg_lbm *h, int32_t x0, int32_t y0, int32_t z0, int32_t bx
                       void *host);
 
 /* Copy the inlet velocity of the last completed step (3*nz*ny floats, lattice
- * units, layout u[c][z][y]) to host memory. */
+ * units, layout u[c][z][y]) to host memory owned by the caller (waits for the
+ * handle's stream).  Errors: STG_ERR_INVALID (NULL), STG_ERR_TIMEOUT,
+ * STG_ERR_CUDA. */
 int stg_lbm_get_inlet(stg_lbm *h, float *host_u);
 
-/* Device pointer of the current populations and the inlet plane (valid until
- * the next step / destroy); for zero-copy inspection by the caller. */
+/* Device pointer of the current populations and the inlet plane of the last
+ * completed step (valid until the next step / destroy; owned by the library,
+ * never freed by the caller); for zero-copy inspection, ordered on the
+ * handle's stream.  Either output may be NULL.  Errors: STG_ERR_INVALID. */
 int stg_lbm_device_state(stg_lbm *h, void **pops, float **inlet_u);
 
+/* Derived setup scalars and the device memory held (stg_info).
+ * Errors: STG_ERR_INVALID (NULL). */
 int stg_lbm_info(const stg_lbm *h, stg_info *out);
 
 /* Launch tile of the plain (non-sampling) steps of the vector step kernels
