@@ -176,15 +176,15 @@ def aggregate_ranks(ms_local, cells_per_rank, steps, dist=None, device="cpu"):
     return ms, cells * steps / (ms * 1e-3) / 1e6
 
 
-def _oracle_single_thread(workload, storage, ny=16, steps=1):
+def _oracle_single_thread(workload, storage, ny=16, steps=1, extra=None):
     """The oracle on one host thread (a child process with OMP_NUM_THREADS=1):
     `steps` steps of an nx x ny x nz slice of the workload (full streamwise
     length and span, fewer wall-normal rows)."""
     code = ("import sys, time, json; sys.path.insert(0, %r); import oracle; from workloads import case; "
-            "c = case(%r).with_(storage=%r, ny=%d); s = oracle.Sim.from_case(c); t0 = time.perf_counter(); "
+            "c = case(%r).with_(storage=%r, ny=%d, **%r); s = oracle.Sim.from_case(c); t0 = time.perf_counter(); "
             "s.step(%d); dt = time.perf_counter() - t0; "
             "print(json.dumps({'value': c.cells * %d / dt / 1e6, 'threads': oracle.threads(), "
-            "'shape': [c.nx, c.ny, c.nz]}))") % (ROOT, workload, storage, ny, steps, steps)
+            "'shape': [c.nx, c.ny, c.nz]}))") % (ROOT, workload, storage, ny, dict(extra or {}), steps, steps)
     try:
         out = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, OMP_NUM_THREADS="1"),
                              capture_output=True, text=True, timeout=600)
@@ -196,12 +196,13 @@ def _oracle_single_thread(workload, storage, ny=16, steps=1):
             "sample": f"{steps} step of a {nx}x{ny_}x{nz} slice of the {workload} channel (FP64, one thread)"}
 
 
-def cpu_baseline(workload, storage, steps):
+def cpu_baseline(workload, storage, steps, extra=None):
     """The CPU FP64 oracle, as it stands, on a bounded sample of the workload:
-    all host cores (OpenMP over z), plus the same oracle on one thread."""
+    all host cores (OpenMP over z), plus the same oracle on one thread.
+    `extra`: case fields of the variant (collision, sponge)."""
     import oracle
     from workloads import case
-    c = case(workload).with_(storage=storage)
+    c = case(workload).with_(storage=storage, **dict(extra or {}))
     sim = oracle.Sim.from_case(c)
     t0 = time.perf_counter()
     sim.step(steps)
@@ -209,7 +210,7 @@ def cpu_baseline(workload, storage, steps):
     del sim
     return {"value": c.cells * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
             "sample": f"{steps} full steps of the {workload} lattice (FP64, OpenMP over z)", "seconds": dt,
-            "single_thread": _oracle_single_thread(workload, storage)}
+            "single_thread": _oracle_single_thread(workload, storage, extra=extra)}
 
 
 def run_reference(args):
@@ -245,6 +246,15 @@ def run_reference(args):
                              "sample": sample},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _variant(c, args):
+    """The workload with the --collision / --sponge choices applied (sponge:
+    0.4 delta with delta = ny / 2, K = 1000, p = 3)."""
+    c = c.with_(collision=args.collision)
+    if args.sponge:
+        c = c.with_(sponge_len=0.4 * c.ny / 2, sponge_K=1000.0, sponge_p=3.0)
+    return c
 
 
 def fp16_companion(c, args):
@@ -288,7 +298,7 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    c = case(args.workload).with_(storage=args.storage)
+    c = _variant(case(args.workload).with_(storage=args.storage), args)
     ch = Channel.from_case(c, check_every=100, mass_tol=0.5, seed=rank_seed(c.seed, rank))
     stream = ch.stream
 
@@ -357,14 +367,16 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     bpc = BYTES_PER_CELL[args.storage]
     achieved = bpc * c.cells / (ms_step * 1e-3) / 1e9
-    traffic = _traffic(args.workload, args.storage)
+    # the committed counters were taken on the default variant
+    traffic = _traffic(args.workload, args.storage) if (args.collision == "regularized" and not args.sponge) else None
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "storage": args.storage, "cells": c.cells, "lattice": "D3Q19",
                    "tile": list(tile),
-                   "collision": c.collision, "stg_modes": c.n_modes, "stats_every": c.stats_every,
+                   "collision": c.collision, "sponge_len": c.sponge_len, "stg_modes": c.n_modes,
+                   "stats_every": c.stats_every,
                    "l2": "inputs larger than L2 (lattice %.2f GB)" % (2 * 19 * c.cells * bpc / 38 / 1e9),
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -380,7 +392,9 @@ def run_ours(args):
     if args.storage == "fp32" and not args.no_companion:
         line["fp16s_companion"] = fp16_companion(c, args)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, args.storage, args.cpu_steps)
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.storage, args.cpu_steps,
+                                            extra=dict(collision=c.collision, sponge_len=c.sponge_len,
+                                                       sponge_K=c.sponge_K, sponge_p=c.sponge_p))
         line["cpu_baseline"].pop("seconds", None)
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -483,6 +497,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="", help="launch tile 'layout,zc,wall_zc' instead of the autotuner's")
     ap.add_argument("--no-companion", action="store_true", help="skip the FP16-storage companion run")
+    ap.add_argument("--collision", choices=["regularized", "bgk"], default="regularized",
+                    help="bulk collision: regularized BGK (default) or plain BGK")
+    ap.add_argument("--sponge", action="store_true",
+                    help="sponge zone of 0.4 delta before the outlet (K = 1000, p = 3, as in the paper's channel)")
     ap.add_argument("--members", type=int, default=64, help="ensemble workload: channels in the batch")
     ap.add_argument("--jobs", type=int, default=60, help="serve workload: jobs in the stream")
     ap.add_argument("--steps-scale", type=float, default=0.1, help="serve workload: scale of the step counts")
