@@ -322,10 +322,21 @@ def run_ours(args):
         sampler.start()
         time.sleep(0.3)
     barrier()
+    if args.probes > 0:
+        # probe series of the paper's post-processing (B_uu, T_t): random cells, seeded
+        prng = np.random.default_rng(1234 + rank)
+        xyz = np.stack([prng.integers(0, n, args.probes) for n in (c.nx, c.ny, c.nz)], axis=1).astype(np.int32)
+        ch.set_probes(xyz)
+        ch.step_probed(args.steps)  # untimed: allocates the series buffer before the timed region
+        torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    ch.step(args.steps)
+    if args.probes > 0:
+        series = ch.step_probed(args.steps)  # synchronises; ends with the series' copy to the host
+        assert series.shape == (args.steps, args.probes, 3)
+    else:
+        ch.step(args.steps)
     e1.record(stream)
     e1.synchronize()
     barrier()
@@ -375,7 +386,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "storage": args.storage, "cells": c.cells, "lattice": "D3Q19",
                    "tile": list(tile),
-                   "collision": c.collision, "sponge_len": c.sponge_len, "stg_modes": c.n_modes,
+                   "collision": c.collision, "sponge_len": c.sponge_len, "probes": args.probes,
+                   "stg_modes": c.n_modes,
                    "stats_every": c.stats_every,
                    "l2": "inputs larger than L2 (lattice %.2f GB)" % (2 * 19 * c.cells * bpc / 38 / 1e9),
                    "parallelism": f"replicas x{ws}"},
@@ -386,7 +398,7 @@ def run_ours(args):
                      "inlet_kernel_ms": ms_inlet},
         "hbm_frac_of_step": bpc * c.cells * args.steps / (ms * 1e-3) / 1e9 / peak,
         "e2e": e2e,
-        "gpu_launches": _launches(c, args.warmup, args.steps),
+        "gpu_launches": _launches(c, args.warmup, args.steps) + (args.steps if args.probes > 0 else 0),
         "clocks": clocks,
     }
     if args.storage == "fp32" and not args.no_companion:
@@ -499,6 +511,8 @@ def main():
     ap.add_argument("--no-companion", action="store_true", help="skip the FP16-storage companion run")
     ap.add_argument("--collision", choices=["regularized", "bgk"], default="regularized",
                     help="bulk collision: regularized BGK (default) or plain BGK")
+    ap.add_argument("--probes", type=int, default=0,
+                    help="time the steps through step_probed with this many velocity probes (seeded random cells)")
     ap.add_argument("--sponge", action="store_true",
                     help="sponge zone of 0.4 delta before the outlet (K = 1000, p = 3, as in the paper's channel)")
     ap.add_argument("--members", type=int, default=64, help="ensemble workload: channels in the batch")
