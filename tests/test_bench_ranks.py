@@ -69,3 +69,19 @@ def test_launch_count_includes_statistics_reductions():
     assert bench._launches(c.with_(stats_every=0), 5, 10) == 30
     odd = c.with_(nx=767)
     assert bench._launches(odd, 0, 20) == 3 * 20
+
+
+def test_bench_variants():
+    """--collision / --sponge: the paper's sponge is 0.4 delta (delta = ny / 2)
+    with K = 1000 and p = 3; defaults leave the workload unchanged."""
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    from workloads import case
+    c = case("channel_768x128x192")
+    same = bench._variant(c, argparse.Namespace(collision="regularized", sponge=False))
+    assert same.collision == "regularized" and same.sponge_len == 0.0
+    v = bench._variant(c, argparse.Namespace(collision="bgk", sponge=True))
+    assert v.collision == "bgk"
+    assert abs(v.sponge_len - 0.4 * 128 / 2) < 1e-12 and v.sponge_K == 1000.0 and v.sponge_p == 3.0
+    assert (v.nx, v.ny, v.nz) == (c.nx, c.ny, c.nz)
