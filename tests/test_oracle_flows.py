@@ -138,3 +138,27 @@ def test_bruteforce_periodic_force():
         s.step(1)
         ref = np.array(bf_step(ref, (4, 3, 5), D3Q19_ORDER, 0.57, 0.02, F, None, bc_x="periodic"))
     np.testing.assert_allclose(s.pops(), ref, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("every,chunks", [(5, (50,)), (5, (7, 5, 38)), (3, (1, 1, 20)), (1, (4,))])
+def test_plug_flow_statistics_accumulation(every, chunks):
+    """Running statistics (eqs. y_plus, v_rms: time- and span-averaged u and
+    u u): in the uniform plug flow every sampled step adds nz U to sum u_x and
+    nz U^2 to sum u_x u_x of each (x, y), nothing to the other sums, and a
+    sample is taken after step t exactly when (t + 1) is a multiple of the
+    sampling period, however the steps are split into calls."""
+    nx, ny, nz = 12, 16, 4
+    prof = _plug_profile(10.0)
+    s = O.Sim(nx, ny, nz, tau0=0.55, c_smag=0.01, bc_x="stg", bc_y="periodic", profile=prof,
+              n_modes=16, t_filter=3.0, mach_target=0.05, stats_every=every)
+    U = s.scalars()["U_b"]
+    total = 0
+    for k in chunks:
+        s.step(k)
+        total += k
+        m, r, n = s.stats()
+        assert n == total // every
+        np.testing.assert_allclose(m[0], n * nz * U, rtol=1e-13, atol=1e-300)
+        np.testing.assert_allclose(m[1:], 0.0, atol=1e-15 * nz * max(n, 1))
+        np.testing.assert_allclose(r[0], n * nz * U * U, rtol=1e-13, atol=1e-300)
+        np.testing.assert_allclose(r[1:], 0.0, atol=1e-15 * nz * max(n, 1))
