@@ -386,8 +386,8 @@ namespace host {
 cudaError_t enqueue_step(stg_lbm *h, int parity, bool stats)
 {
     const stg::InletArgs in = inlet_args(h, parity);
-    return stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, stats,
-                            h->has_tmap ? h->tmap[parity] : nullptr, h->stream, h->side, h->ev_fork, h->ev_join,
+    return stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, stats, h->stream, h->side,
+                            h->ev_fork, h->ev_join,
                             h->inout ? &in : nullptr);
 }
 
@@ -689,7 +689,7 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
     const int nx = domain->nx, ny = domain->ny, nz = domain->nz;
     if (const char *ev = std::getenv("STG_LBM_INTERIOR")) {
         const std::string v(ev);
-        h->interior = v == "scalar" ? 1 : v == "pair" ? 2 : v == "tma" ? 3 : 0;
+        h->interior = v == "scalar" ? 1 : v == "pair" ? 2 : 0;
     }
     h->P = (size_t)nx * ny * nz;
     h->elem = domain->storage == STG_FP32 ? 4 : 2;
@@ -745,15 +745,6 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
     if (h->inout) {
         rc = build_inlet(h, rans, seed);
         if (rc) return bail(rc);
-    }
-    e = stg::tma_prepare();
-    if (e != cudaSuccess) {
-        cuda_fail(h, e, "tma_prepare");
-        return bail(STG_ERR_CUDA);
-    }
-    if (stg::tma_usable(nx, domain->storage)) {
-        h->has_tmap = stg::tma_encode(h->tmap[0], h->lat[0], domain->storage, nx, ny, nz) == 0 &&
-                      stg::tma_encode(h->tmap[1], h->lat[1], domain->storage, nx, ny, nz) == 0;
     }
     e = stg::launch_init_equilibrium(h->lat[0], domain->storage, nx, ny, nz, h->inout ? h->u_int : nullptr,
                                      h->stream);
@@ -843,8 +834,7 @@ int stg_lbm_step_timed(stg_lbm *h, int64_t n, double *ms_step, double *ms_inlet)
         if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], h->stream);
         if (e == cudaSuccess)
             e = stg::launch_step(step_args(h, parity), h->d.storage, h->d.collision, is_stats_step(h, h->t),
-                                 h->has_tmap ? h->tmap[parity] : nullptr, h->stream, h->side, h->ev_fork,
-                                 h->ev_join);
+                                 h->stream, h->side, h->ev_fork, h->ev_join);
         if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], h->stream);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "timed step launch");
         else h->t += 1;
@@ -886,7 +876,7 @@ int stg_lbm_stats(stg_lbm *h, stg_stats *out)
     CK(cudaMemcpy(&kerr, &h->ctl->err, sizeof kerr, cudaMemcpyDeviceToHost));
     if (kerr) {
         h->sticky = STG_ERR_TIMEOUT;
-        return fail(h, STG_ERR_TIMEOUT, "a kernel's bounded wait for its staged copies expired");
+        return fail(h, STG_ERR_TIMEOUT, "a kernel set its error bit (a bounded device-side wait expired)");
     }
     double mass = 0.0;
     int rc2 = compute_mass(h, &mass);
@@ -1160,8 +1150,7 @@ cudaError_t trial_pass(stg_lbm *h, const stg_tile &tile, cudaStream_t s)
     stg::StepArgs a = step_args(h, parity);
     h->tile = keep;
     a.stats_every = 0;  // the edge kernel samples on its own otherwise
-    return stg::launch_step(a, h->d.storage, h->d.collision, false, h->has_tmap ? h->tmap[parity] : nullptr, s,
-                            h->side, h->ev_fork, h->ev_join);
+    return stg::launch_step(a, h->d.storage, h->d.collision, false, s, h->side, h->ev_fork, h->ev_join);
 }
 
 int apply_tile(stg_lbm *h, const stg_tile &tile)

@@ -47,8 +47,6 @@ struct stg_lbm {
     double *h_pinned = nullptr;  // [0]: last checked mass
     cudaEvent_t ev_check = nullptr, ev_done = nullptr;
     cudaStream_t side = nullptr;                       // branch for the edge kernel
-    alignas(64) unsigned char tmap[2][128];            // tensor maps of the two lattices (CUtensorMap)
-    bool has_tmap = false;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool check_pending = false;
     int64_t t = 0, t0_stats = 0;
@@ -62,7 +60,7 @@ struct stg_lbm {
     int block_steps = 16;
     stg_info info{};
     double timeout_s = 900.0;
-    int interior = 0;  // STG_LBM_INTERIOR=scalar|pair|tma overrides the interior kernel choice
+    int interior = 0;  // STG_LBM_INTERIOR=scalar|pair overrides the interior kernel choice
     stg_tile tile{1, 8, 24, 0};
     stg_batch *batch = nullptr;  // the batch this lattice belongs to (its steps run there)
 };

@@ -14,7 +14,7 @@ namespace stg {
 struct StepCtl {
     long long t[2];
     long long t0_filter;  // step at which the temporal filter restarts
-    unsigned long long err; // error bits set by kernels (1: bounded wait on an mbarrier expired)
+    unsigned long long err; // error bits set by kernels (none of the current kernels sets one)
 };
 
 struct StepArgs {
@@ -30,7 +30,7 @@ struct StepArgs {
     const void *srcy[19];
     void *dstp[19];
     int il, ir;             // 32-wide x chunks [il, ir) of rows 1..ny-2 belong to the interior kernel
-    int interior;           // interior kernel: 0 best available, 1 one cell per thread, 2 cell pairs, 3 TMA-staged
+    int interior;           // interior kernel: 0 best available, 1 one cell per thread, 2 cell pairs
     // tile of the plain (non-sampling) vector launches: layout 0 = 8 z-warps on one 64-cell x chunk,
     // layout 1 = 4 x-warps (256 cells) walking z together; zc / wall_zc = z planes per block of the
     // rows 1..ny-2 / wall-row launch (0: the whole z column)
@@ -88,9 +88,8 @@ struct MassArgs {
 // launchers (return the launch status)
 // `stats` must be true exactly on sampling steps ((t + 1) % stats_every == 0);
 // the host tracks t and decides.
-// tensor_map: the source lattice's tensor map (nullptr: no TMA-staged kernel)
 // inlet: the inlet kernel for the next step's plane (NULL: none), launched on the branch
-cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, const void *tensor_map,
+cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats,
                         cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join,
                         const InletArgs *inlet = nullptr);
 cudaError_t launch_inlet(const InletArgs &a, cudaStream_t s);
@@ -103,17 +102,6 @@ cudaError_t launch_mass(const MassArgs &a, cudaStream_t s);
 // velocity of n cells (xyz: device int triples) of a stored lattice into out[3 n]
 cudaError_t launch_probe(const void *src, int storage, size_t P, int nx, int ny, int n, const int *xyz, float Fx,
                          float Fy, float Fz, float *out, cudaStream_t s);
-
-// TMA-staged interior kernel (tma_kernel.cu): usable when a lattice row is a
-// whole number of 16-byte units; tma_prepare() raises the kernels' dynamic
-// shared-memory limit (call once before launching or capturing).
-bool tma_usable(int nx, int storage);
-cudaError_t tma_prepare();
-// encode the tensor map of one stored lattice into map_out (a 64-byte aligned
-// CUtensorMap); 0 on success
-int tma_encode(void *map_out, const void *lattice, int storage, int nx, int ny, int nz);
-cudaError_t launch_tma(const StepArgs &a, const void *tensor_map, int gx, int gy, int storage, int collision,
-                       bool stats, cudaStream_t s);
 
 // Upper bound of the mass-partial slots of one step pass over every tile
 // that set_tile accepts (z chunks of at least MIN_ZC planes).

@@ -727,7 +727,7 @@ int step_grid_blocks(int nx, int ny, int nz)
 // How a pass covers the lattice.
 //  vector split: vector kernel on rows 1..ny-2 and on rows {0, ny-1} (all x,
 //                inlet/outlet nodes included);
-//  scalar split: interior kernel (one cell per thread, or TMA-staged) on the
+//  scalar split: interior kernel (one cell per thread) on the
 //                32-wide chunks [1, nxc-1) of rows 1..ny-2, edge kernel on the
 //                rest.
 struct Split {
@@ -761,7 +761,7 @@ static Split split_of(const StepArgs &a, int cpl)
 
 // Returns true when the pass left z-group statistics in a.stat_part.
 template <typename S, bool REG, bool FORCE, bool SP>
-static bool launch_forced(StepArgs a, const Split &sp, bool stats, const void *tmap, cudaStream_t s,
+static bool launch_forced(StepArgs a, const Split &sp, bool stats, cudaStream_t s,
                           cudaStream_t side)
 {
     const dim3 block(BX, BZ);
@@ -811,9 +811,7 @@ static bool launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
         else lbm_vec_zc_kernel<S, REG, FORCE, 0, true, SP><<<ge, block, 0, side>>>(ae);
         return stats;
     }
-    const bool tma = !SP && a.interior == 3 && tmap && sp.gx > 0 && sp.gy > 0 && (sp.ir - sp.il) % 2 == 0 &&
-                     a.nx % 2 == 0 && 19.0 * a.nx * a.ny * a.nz < 4294967296.0 && tma_usable(a.nx, storage);
-    const int n_in = sp.gy > 0 ? (tma ? (sp.ir - sp.il) / 2 : sp.gx) * sp.gy : 0;
+    const int n_in = sp.gy > 0 ? sp.gx * sp.gy : 0;
     a.il = sp.il;
     a.ir = sp.ir;
     a.total_blocks = (unsigned)(n_in + sp.n_edge);
@@ -823,22 +821,21 @@ static bool launch_forced(StepArgs a, const Split &sp, bool stats, const void *t
     ae.bump_t = 1;
     lbm_edge_kernel<S, REG, FORCE, SP><<<sp.n_edge, block, 0, side>>>(ae);
     if (n_in > 0) {
-        if (tma) launch_tma(ai, tmap, (sp.ir - sp.il) / 2, sp.gy, storage, REG ? 0 : 1, stats, s);
-        else lbm_step_kernel<S, REG, FORCE, SP><<<dim3(sp.gx, sp.gy), block, 0, s>>>(ai);
+        lbm_step_kernel<S, REG, FORCE, SP><<<dim3(sp.gx, sp.gy), block, 0, s>>>(ai);
     }
     return false;
 }
 
 template <typename S, bool REG>
-static bool launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaStream_t s, cudaStream_t side)
+static bool launch_typed(const StepArgs &a0, bool stats, cudaStream_t s, cudaStream_t side)
 {
     const Split sp = split_of(a0, VecOf<S>::CPL);
     StepArgs a = a0;
     a.bump_t = 0;
     // the sponge is only compiled for unforced lattices (the host refuses a sponge with a force)
-    if (a.spf) return launch_forced<S, REG, false, true>(a, sp, stats, tmap, s, side);
-    if (a.has_force) return launch_forced<S, REG, true, false>(a, sp, stats, tmap, s, side);
-    return launch_forced<S, REG, false, false>(a, sp, stats, tmap, s, side);
+    if (a.spf) return launch_forced<S, REG, false, true>(a, sp, stats, s, side);
+    if (a.has_force) return launch_forced<S, REG, true, false>(a, sp, stats, s, side);
+    return launch_forced<S, REG, false, false>(a, sp, stats, s, side);
 }
 
 // One fused step pass.  With a side stream and two events the wall rows (or
@@ -846,7 +843,7 @@ static bool launch_typed(const StepArgs &a0, bool stats, const void *tmap, cudaS
 // with the interior (both read only the previous lattice and write disjoint
 // cells); `s` waits for both.  `inlet`
 // (may be NULL) computes the next step's inlet plane on the branch.
-cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats, const void *tmap,
+cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats,
                         cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, const InletArgs *inlet)
 {
     cudaError_t e = cudaSuccess;
@@ -861,11 +858,11 @@ cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stat
     if (inlet && (e = launch_inlet(*inlet, es)) != cudaSuccess) return e;
     bool reduce = false;
     if (storage == 0) {
-        if (collision == 0) reduce = launch_typed<float, true>(a, stats, tmap, s, es);
-        else reduce = launch_typed<float, false>(a, stats, tmap, s, es);
+        if (collision == 0) reduce = launch_typed<float, true>(a, stats, s, es);
+        else reduce = launch_typed<float, false>(a, stats, s, es);
     } else {
-        if (collision == 0) reduce = launch_typed<__half, true>(a, stats, tmap, s, es);
-        else reduce = launch_typed<__half, false>(a, stats, tmap, s, es);
+        if (collision == 0) reduce = launch_typed<__half, true>(a, stats, s, es);
+        else reduce = launch_typed<__half, false>(a, stats, s, es);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (forked) {
