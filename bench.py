@@ -1,18 +1,26 @@
 """Throughput benchmark of the STG-LBM hot path (MLUPS and HBM roofline).
 
-One step = the STG inlet kernel plus the fused stream/collide kernel over the
-whole lattice (with FP64 statistics every 10 steps), i.e. one pass of the
-whole hot path.  Default workload: the Re_tau = 180 channel on a 768x128x192
-D3Q19 FP32 lattice (h = 64, 200 STG modes), inputs resident in HBM, lattice
-(2.9 GB) far larger than L2.
+One step = the STG inlet kernel plus the fused stream/collide pass over the
+whole lattice (FP64 statistics every 10 steps, FP64 mass check every 100),
+i.e. one pass of the whole hot path.  Default workload: the refined Re_tau =
+180 channel on a 1536x256x384 D3Q19 lattice (h = 128, 151M cells, 200 STG
+modes) with populations stored as shifted FP16 (f - w_i, FP32 arithmetic),
+inputs resident in HBM, lattice (5.7 GB) far larger than L2.  The same line
+carries the FP32-storage companion on the same lattice, the end-to-end figure
+through the public API, the CPU oracle on a bounded sample, and two
+sub-objects: the batched ensemble (64 channels) and the served job stream
+(Poisson arrivals, continuous batching, p50/p99 latency).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --workload ensemble [--members 64] [--steps K]   (batched ensemble)
-  python bench.py --workload serve [--jobs 60] [--steps-scale 0.1]   (served stream)
+  python bench.py --storage fp32 --workload channel_768x128x192 --no-extras
+  python bench.py --workload ensemble [--members 64] [--steps K]   (batched ensemble alone)
+  python bench.py --workload serve [--jobs 100] [--serve-steps-scale 0.25]   (served stream alone)
 
 N > 1 runs one independent channel per GPU (weak scaling, no collective on
-the data path).  ``--impl reference`` times the CPU FP64 oracle on the host
-cores instead (bounded sample).  Prints one JSON line (rank 0).
+the data path); the companion runs on rank 0, the CPU baseline and the
+ensemble and served sub-objects only at N = 1.  ``--impl reference`` times the
+CPU FP64 oracle on the host cores instead (bounded sample).  Prints one JSON
+line (rank 0).
 """
 from __future__ import annotations
 
@@ -176,7 +184,7 @@ def aggregate_ranks(ms_local, cells_per_rank, steps, dist=None, device="cpu"):
     return ms, cells * steps / (ms * 1e-3) / 1e6
 
 
-def _oracle_single_thread(workload, storage, ny=16, steps=1, extra=None):
+def _oracle_single_thread(workload, storage, ny=8, steps=1, extra=None):
     """The oracle on one host thread (a child process with OMP_NUM_THREADS=1):
     `steps` steps of an nx x ny x nz slice of the workload (full streamwise
     length and span, fewer wall-normal rows)."""
@@ -196,46 +204,53 @@ def _oracle_single_thread(workload, storage, ny=16, steps=1, extra=None):
             "sample": f"{steps} step of a {nx}x{ny_}x{nz} slice of the {workload} channel (FP64, one thread)"}
 
 
-def cpu_baseline(workload, storage, steps, extra=None):
-    """The CPU FP64 oracle, as it stands, on a bounded sample of the workload:
-    all host cores (OpenMP over z), plus the same oracle on one thread.
-    `extra`: case fields of the variant (collision, sponge)."""
+def _slice_rows(full, budget_cells, steps):
+    """Wall-normal rows of a bounded oracle sample: the full streamwise length
+    and span (so the per-cell share of inlet-generator work, N / nx, and the
+    OpenMP split over z are those of the full channel), at least 2 rows (walls
+    on both), about budget_cells cell updates over `steps` steps."""
+    return max(2, min(full.ny, int(budget_cells / (steps * full.nx * full.nz))))
+
+
+def cpu_baseline(workload, storage, steps, budget_cells, extra=None):
+    """The CPU FP64 oracle, as it stands, on a bounded sample of the workload
+    (a slice of the channel with fewer wall-normal rows) on all host cores
+    (OpenMP over z), plus the same oracle on one thread.  `extra`: case
+    fields of the variant (collision, sponge)."""
     import oracle
     from workloads import case
-    c = case(workload).with_(storage=storage, **dict(extra or {}))
+    full = case(workload).with_(storage=storage, **dict(extra or {}))
+    c = full.with_(ny=_slice_rows(full, budget_cells, steps))
     sim = oracle.Sim.from_case(c)
     t0 = time.perf_counter()
     sim.step(steps)
     dt = time.perf_counter() - t0
     del sim
     return {"value": c.cells * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{steps} full steps of the {workload} lattice (FP64, OpenMP over z)", "seconds": dt,
-            "single_thread": _oracle_single_thread(workload, storage, extra=extra)}
+            "sample": f"{steps} steps of a {c.nx}x{c.ny}x{c.nz} slice of the {workload} channel "
+                      f"(FP64, OpenMP over z, inlet, outlet, walls, {c.n_modes} STG modes)",
+            "seconds": dt, "single_thread": _oracle_single_thread(workload, storage, extra=extra)}
 
 
 def run_reference(args):
     """Reference arm: the CPU FP64 oracle on the host cores.  Each step is one
-    oracle step of a bounded sample of the workload: the full streamwise
-    length and span (so the share of inlet-generator work per cell, N / nx,
-    and the OpenMP split over z are those of the full channel) with fewer
-    wall-normal rows (at least 2, walls on both), chosen so that warm-up +
-    timed steps stay within about a minute of CPU time."""
+    oracle step of a bounded sample of the workload (a slice with fewer
+    wall-normal rows), sized so that warm-up + timed steps stay within about
+    a minute of CPU time."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     import oracle
     from workloads import case
     full = case(args.workload)
-    budget_cells = 3.0e8  # cell updates over the whole run
-    ny = max(2, min(full.ny, int(budget_cells / ((args.steps + args.warmup) * full.nx * full.nz))))
-    c = full.with_(ny=ny)
+    c = full.with_(ny=_slice_rows(full, 3.0e8, args.steps + args.warmup))
     sim = oracle.Sim.from_case(c)
     sim.step(args.warmup)
     t0 = time.perf_counter()
     sim.step(args.steps)
     t = time.perf_counter() - t0
     value = c.cells * args.steps / t / 1e6
-    sample = (f"{args.steps} timed steps (+{args.warmup} warm-up) of a {c.nx}x{ny}x{c.nz} slice of the "
+    sample = (f"{args.steps} timed steps (+{args.warmup} warm-up) of a {c.nx}x{c.ny}x{c.nz} slice of the "
               f"{args.workload} channel (inlet, outlet, walls, {c.n_modes} STG modes)")
     line = {"impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
@@ -257,53 +272,38 @@ def _variant(c, args):
     return c
 
 
-def fp16_companion(c, args):
-    """The same channel with populations stored as shifted FP16, timed the
-    same way (autotuned tile, W warm-up steps, K steps between CUDA events),
-    so one bench line carries the FP16-storage vs FP32 comparison."""
+RATED_HBM_GBS = 7900.0  # nominal HBM3e bandwidth of the part (context beside the measured copy peak)
+
+
+def roofline(bpc, cells, ms_step, ms_inlet, traffic, kernel):
+    """Roofline object of one step pass: algorithmic bytes (bpc per cell) over
+    the event-timed pass, against the measured copy bandwidth and, for
+    context, the rated HBM bandwidth; with the ncu DRAM traffic of the pass
+    (when the committed counters match the kernel source) also the bandwidth
+    that traffic implies."""
+    peak, peak_kind = _peaks()
+    achieved = bpc * cells / (ms_step * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": kernel, "kernel_ms": ms_step, "bytes_per_cell": bpc,
+            "peak_source": f"{peak_kind} hbm_gbs (copy)", "rated_peak": RATED_HBM_GBS,
+            "frac_of_rated": achieved / RATED_HBM_GBS,
+            "traffic_gbs": (traffic / (ms_step * 1e-3) / 1e9) if traffic else None,
+            "inlet_kernel_ms": ms_inlet}
+
+
+STEP_KERNEL = "lbm_vec_zc_kernel (rows 1..ny-2, inlet and outlet nodes included) + wall rows: one step pass"
+
+
+def measure_channel(c, args, rank=0, dist=None, seed=None, sample_clocks=True):
+    """One channel timed the bench's way: the library's autotuned launch tile
+    (or --tile), W warm-up steps, then K steps between CUDA events on the
+    channel's stream with a barrier and a device synchronisation on both
+    sides; then the device time of single step passes (stg_lbm_step_timed).
+    Returns the timings, clocks and throughput (aggregated over ranks when
+    `dist` is given)."""
     import torch
     from paper_2205_02774_gb300.channel import Channel
-    c16 = c.with_(storage="fp16s")
-    ch = Channel.from_case(c16, check_every=100, mass_tol=0.5)
-    tile = ch.autotune(20)
-    ch.step(args.warmup)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(ch.stream)
-    ch.step(args.steps)
-    e1.record(ch.stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    rc = ch.stats()["rc"]
-    ch.close()
-    peak, _ = _peaks()
-    bpc = BYTES_PER_CELL["fp16s"]
-    return {"storage": "fp16s", "value": c16.cells * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
-            "ms_per_step": ms / args.steps, "hbm_frac_of_step": bpc * c16.cells * args.steps / (ms * 1e-3) / 1e9 / peak,
-            "tile": list(tile), "rc": rc}
-
-
-def run_ours(args):
-    import numpy as np
-    import torch
-    from paper_2205_02774_gb300 import build
-    build()
-    from paper_2205_02774_gb300.channel import Channel
-    from workloads import case
-
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    c = _variant(case(args.workload).with_(storage=args.storage), args)
-    ch = Channel.from_case(c, check_every=100, mass_tol=0.5, seed=rank_seed(c.seed, rank))
-    stream = ch.stream
-
-    # launch tile from the library's autotuner (results do not depend on it),
-    # then warm-up (also initialises graphs, clocks)
+    ch = Channel.from_case(c, check_every=100, mass_tol=0.5, seed=c.seed if seed is None else seed)
     if args.tile:
         tile = tuple(int(v) for v in args.tile.split(","))
         ch.set_tile(*tile)
@@ -317,13 +317,14 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    sampler = ClockSampler(local) if rank == 0 else None
+    sampler = ClockSampler(torch.cuda.current_device()) if (rank == 0 and sample_clocks) else None
     if sampler:
         sampler.start()
         time.sleep(0.3)
     barrier()
     if args.probes > 0:
         # probe series of the paper's post-processing (B_uu, T_t): random cells, seeded
+        import numpy as np
         prng = np.random.default_rng(1234 + rank)
         xyz = np.stack([prng.integers(0, n, args.probes) for n in (c.nx, c.ny, c.nz)], axis=1).astype(np.int32)
         ch.set_probes(xyz)
@@ -331,13 +332,13 @@ def run_ours(args):
         torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    e0.record(ch.stream)
     if args.probes > 0:
         series = ch.step_probed(args.steps)  # synchronises; ends with the series' copy to the host
         assert series.shape == (args.steps, args.probes, 3)
     else:
         ch.step(args.steps)
-    e1.record(stream)
+    e1.record(ch.stream)
     e1.synchronize()
     barrier()
     clocks = sampler.stop() if sampler else None
@@ -345,86 +346,120 @@ def run_ours(args):
     st = ch.stats()
     if st["rc"] != 0:
         raise RuntimeError(f"channel check failed: {st['error']}")
-
-    # dominant kernel: per-launch device time of the fused step kernel
+    # dominant kernel: device time of one step pass (the two step launches)
     ms_step, ms_inlet = ch.step_timed(min(200, max(20, args.steps // 10)))
     ch.close()
     del ch
     torch.cuda.synchronize()
-
-    # end-to-end through the public API with host buffers
-    e2e = None
-    if rank == 0:
-        prof = c.profile()
-        host_in = sum(a.nbytes for a in (prof.y_c, prof.U, prof.k, prof.eps, prof.R))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ch2 = Channel.from_case(c, check_every=100, mass_tol=0.5)
-        ch2.step(args.steps)
-        st2 = ch2.stats()
-        t1 = time.perf_counter()
-        host_out = 9 * c.nx * c.ny * 8 + 16
-        ch2.close()
-        e2e = {"value": c.cells * args.steps / (t1 - t0) / 1e6, "unit": "MLUPS",
-               "h2d_bytes_per_step": host_in / args.steps, "d2h_bytes_per_step": host_out / args.steps,
-               "seconds": t1 - t0, "includes": "create (host profile upload, tables, init, graph capture) + "
-                                               "step(K) + stats (FP64 sums to host) + destroy"}
-        assert st2["rc"] == 0
-
-    if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
-        return
-    peak, peak_kind = _peaks()
-    bpc = BYTES_PER_CELL[args.storage]
-    achieved = bpc * c.cells / (ms_step * 1e-3) / 1e9
-    # the committed counters were taken on the default variant
-    traffic = _traffic(args.workload, args.storage) if (args.collision == "regularized" and not args.sponge) else None
-    line = {
-        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "storage": args.storage, "cells": c.cells, "lattice": "D3Q19",
-                   "tile": list(tile),
-                   "collision": c.collision, "sponge_len": c.sponge_len, "probes": args.probes,
-                   "stg_modes": c.n_modes,
-                   "stats_every": c.stats_every,
-                   "l2": "inputs larger than L2 (lattice %.2f GB)" % (2 * 19 * c.cells * bpc / 38 / 1e9),
-                   "parallelism": f"replicas x{ws}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "lbm_vec_zc_kernel (rows 1..ny-2, inlet and outlet nodes included) + wall rows: one step pass",
-                     "kernel_ms": ms_step,
-                     "bytes_per_cell": bpc, "peak_source": f"{peak_kind} hbm_gbs (copy)",
-                     "inlet_kernel_ms": ms_inlet},
-        "hbm_frac_of_step": bpc * c.cells * args.steps / (ms * 1e-3) / 1e9 / peak,
-        "e2e": e2e,
-        "gpu_launches": _launches(c, args.warmup, args.steps) + (args.steps if args.probes > 0 else 0),
-        "clocks": clocks,
-    }
-    if args.storage == "fp32" and not args.no_companion:
-        line["fp16s_companion"] = fp16_companion(c, args)
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, args.storage, args.cpu_steps,
-                                            extra=dict(collision=c.collision, sponge_len=c.sponge_len,
-                                                       sponge_K=c.sponge_K, sponge_p=c.sponge_p))
-        line["cpu_baseline"].pop("seconds", None)
-    print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    bpc = BYTES_PER_CELL[c.storage]
+    peak, _ = _peaks()
+    return {"value": value, "ms": ms, "ms_per_step": ms / args.steps, "tile": list(tile), "clocks": clocks,
+            "ms_step": ms_step, "ms_inlet": ms_inlet,
+            "hbm_frac_of_step": bpc * c.cells * args.steps / (ms * 1e-3) / 1e9 / peak}
 
 
-def run_ensemble(args):
-    """Batched ensemble: 64 independent channels (h from {16, 24, 32, 48, 64},
-    Re_tau from {180, 395}, seeds 1..64) advanced by the batch executor, one
-    CUDA-graph launch per block of steps; the batch's tile comes from the
-    autotuner.  Prints one JSON line (whole-batch MLUPS)."""
+def end_to_end(c, steps):
+    """The same metric end to end through the public API with host buffers:
+    create (RANS profile uploaded from host memory, device allocation from an
+    emptied caching allocator, inlet tables, initial state, graph capture),
+    K steps, the statistics read back to the host (FP64 sums) and destroy."""
+    import torch
+    from paper_2205_02774_gb300.channel import Channel
+    prof = c.profile()
+    host_in = sum(a.nbytes for a in (prof.y_c, prof.U, prof.k, prof.eps, prof.R))
+    torch.cuda.empty_cache()  # create() must allocate its device memory for real
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ch = Channel.from_case(c, check_every=100, mass_tol=0.5)
+    ch.step(steps)
+    st = ch.stats()
+    ch.close()
+    t1 = time.perf_counter()
+    host_out = 9 * c.nx * c.ny * 8 + 16
+    assert st["rc"] == 0, st["error"]
+    return {"value": c.cells * steps / (t1 - t0) / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": host_in / steps, "d2h_bytes_per_step": host_out / steps,
+            "seconds": t1 - t0, "includes": "create (host profile upload, device allocation after emptying the "
+                                            "caching allocator, tables, init, graph capture) + step(K) + stats "
+                                            "(FP64 sums to host) + destroy"}
+
+
+def run_ours(args):
     import torch
     from paper_2205_02774_gb300 import build
     build()
+    from workloads import case
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    c = _variant(case(args.workload).with_(storage=args.storage), args)
+    m = measure_channel(c, args, rank, dist, seed=rank_seed(c.seed, rank))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+
+    # the committed counters were taken on the default variant
+    plain = args.collision == "regularized" and not args.sponge and args.probes == 0
+    traffic = _traffic(args.workload, c.storage) if plain else None
+    line = {
+        "metric": "MLUPS", "value": m["value"], "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "storage": c.storage, "cells": c.cells, "lattice": "D3Q19",
+                   "arithmetic": "fp32", "tile": m["tile"],
+                   "collision": c.collision, "sponge_len": c.sponge_len, "probes": args.probes,
+                   "stg_modes": c.n_modes,
+                   "stats_every": c.stats_every,
+                   "l2": "inputs larger than L2 (lattice %.2f GB)" % (2 * 19 * c.cells * BYTES_PER_CELL[c.storage] / 38 / 1e9),
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roofline(BYTES_PER_CELL[c.storage], c.cells, m["ms_step"], m["ms_inlet"], traffic, STEP_KERNEL),
+        "hbm_frac_of_step": m["hbm_frac_of_step"],
+        "gpu_launches": _launches(c, args.warmup, args.steps) + (args.steps if args.probes > 0 else 0),
+        "clocks": m["clocks"],
+    }
+    line["e2e"] = end_to_end(c, args.steps)
+    if not args.no_companion:
+        # the same channel in the other storage form, timed the same way
+        other = "fp32" if c.storage == "fp16s" else "fp16s"
+        c2 = c.with_(storage=other)
+        m2 = measure_channel(c2, args)
+        t2 = _traffic(args.workload, other) if plain else None
+        line[f"{other}_companion"] = {
+            "storage": other, "value": m2["value"], "unit": "MLUPS", "ms_per_step": m2["ms_per_step"],
+            "hbm_frac_of_step": m2["hbm_frac_of_step"], "tile": m2["tile"], "clocks": m2["clocks"],
+            "roofline": roofline(BYTES_PER_CELL[other], c2.cells, m2["ms_step"], m2["ms_inlet"], t2, STEP_KERNEL),
+            "gpu_launches": _launches(c2, args.warmup, args.steps)}
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, c.storage, args.cpu_steps, args.cpu_cells,
+                                            extra=dict(collision=c.collision, sponge_len=c.sponge_len,
+                                                       sponge_K=c.sponge_K, sponge_p=c.sponge_p))
+        line["cpu_baseline"].pop("seconds", None)
+    if ws == 1 and not args.no_extras:
+        import torch
+        torch.cuda.empty_cache()
+        line["ensemble"] = ensemble_run(args.members, args.ensemble_steps, max(3, min(args.warmup, 20)), "fp32")
+        torch.cuda.empty_cache()
+        line["served"] = serve_run(args.jobs, args.serve_steps_scale)
+    print(json.dumps(line), flush=True)
+
+
+def ensemble_run(members, steps, warmup, storage):
+    """Batched ensemble: `members` independent channels (h from {16, 24, 32,
+    48, 64}, Re_tau from {180, 395}, seeds 1..members) advanced by the batch
+    executor, one CUDA-graph launch per block of steps; the batch's tile from
+    the autotuner.  Whole-batch MLUPS over the whole step (inlet kernels
+    included) and its fraction of the HBM roofline."""
+    import torch
     from paper_2205_02774_gb300.channel import Channel
     from paper_2205_02774_gb300.serving import Batch
     from workloads.serving import ensemble
-    jobs = ensemble(args.members, steps=args.steps, storage=args.storage)
+    jobs = ensemble(members, steps=steps, storage=storage)
     t0 = time.perf_counter()
     chans = [Channel.from_case(j.case, check_every=100, mass_tol=0.5) for j in jobs]
     b = Batch()
@@ -432,15 +467,15 @@ def run_ensemble(args):
         b.add(ch)
     tile = b.autotune(3)
     t_setup = time.perf_counter() - t0
-    b.step(args.warmup)
+    b.step(warmup)
     b.sync()
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(b.stream)
-    b.step(args.steps)
+    b.step(steps)
     e1.record(b.stream)
     e1.synchronize()
     clocks = sampler.stop()
@@ -448,76 +483,102 @@ def run_ensemble(args):
     bad = [i for i, ch in enumerate(chans) if ch.stats()["rc"] != 0]
     cells = sum(ch.cells for ch in chans)
     peak, peak_kind = _peaks()
-    bpc = BYTES_PER_CELL[args.storage]
-    value = cells * args.steps / (ms * 1e-3) / 1e6
-    achieved = bpc * cells * args.steps / (ms * 1e-3) / 1e9
-    line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"ensemble of {len(chans)} channels", "storage": args.storage, "cells": cells,
-                       "members": len(chans), "block_steps": b.block_steps, "tile": tile,
-                       "l2": "inputs larger than L2", "setup_s": t_setup},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "scope": "whole step incl. inlet kernels",
-                         "peak_source": f"{peak_kind} hbm_gbs (copy)"},
-            "failed_members": bad, "clocks": clocks,
-            "gpu_launches": sum(_launches(j.case, args.warmup, args.steps) for j in jobs)}
+    bpc = BYTES_PER_CELL[storage]
+    achieved = bpc * cells * steps / (ms * 1e-3) / 1e9
+    out = {"workload": f"ensemble of {len(chans)} channels", "value": cells * steps / (ms * 1e-3) / 1e6,
+           "unit": "MLUPS", "steps": steps, "warmup": warmup, "ms_per_step": ms / steps, "storage": storage,
+           "cells": cells, "members": len(chans), "block_steps": b.block_steps, "tile": tile, "setup_s": t_setup,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": None, "scope": "whole step incl. inlet kernels",
+                        "peak_source": f"{peak_kind} hbm_gbs (copy)"},
+           "failed_members": bad, "clocks": clocks,
+           "gpu_launches": sum(_launches(j.case, warmup, steps) for j in jobs)}
     b.close()
     for ch in chans:
         ch.close()
-    print(json.dumps(line), flush=True)
+    return out
 
 
-def run_serve(args):
+def serve_run(n_jobs, steps_scale):
     """Served stream: Poisson arrivals (2 jobs/s) of channel jobs of 0.5M-20M
     cells (h = 20..65, aspect 12:2:3), Re_tau from {180, 395}, FP32 or FP16
     storage, own seeds, step counts uniform in [1000, 20000] x steps_scale,
-    admitted by a 150 GB budget into the continuous-batching loop.  Prints one
-    JSON line (jobs/s, aggregate MLUPS, p50/p99 latency)."""
-    from paper_2205_02774_gb300 import build
-    build()
+    admitted by a 150 GB budget into the continuous-batching loop.  Jobs/s,
+    aggregate and offered MLUPS, p50/p99 completion latency."""
+    import torch
     from paper_2205_02774_gb300.serving import serve
     from workloads.serving import poisson_stream
-    sm = max(1, int(round(1000 * args.steps_scale)))
-    jobs = poisson_stream(args.jobs, rate_per_s=2.0, steps_min=sm, steps_max=max(sm, int(round(20000 * args.steps_scale))))
-    sampler = ClockSampler(0)
+    sm = max(1, int(round(1000 * steps_scale)))
+    jobs = poisson_stream(n_jobs, rate_per_s=2.0, steps_min=sm, steps_max=max(sm, int(round(20000 * steps_scale))))
+    sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     results, rep = serve(jobs, hbm_budget_bytes=150e9, check_every=100, mass_tol=0.5)
     clocks = sampler.stop()
     offered = sum(j.case.cells * j.steps for j in jobs) / max(jobs[-1].arrival_s, 1e-9) / 1e6
-    line = {"metric": "jobs/s", "value": rep["jobs_per_s"], "unit": "jobs/s", "n_gpus": 1,
-            "higher_is_better": True, "data": "synthetic", "dtype": "f32",
-            "config": {"workload": f"served stream of {len(jobs)} jobs", "arrival_rate_per_s": 2.0,
-                       "steps_scale": args.steps_scale, "hbm_budget_gb": 150},
+    return {"workload": f"served stream of {len(jobs)} jobs", "value": rep["jobs_per_s"], "unit": "jobs/s",
+            "arrival_rate_per_s": 2.0, "steps_scale": steps_scale, "steps_range": [sm, int(round(20000 * steps_scale))],
+            "hbm_budget_gb": 150,
             "aggregate_mlups": rep["aggregate_mlups"], "offered_mlups": offered,
             "p50_latency_s": rep["p50_latency_s"], "p99_latency_s": rep["p99_latency_s"],
             "mean_latency_s": rep["mean_latency_s"], "wall_s": rep["wall_s"], "completed": rep["completed"],
             "failed": rep["failed"], "peak_active": rep["peak_active"],
             "peak_device_gb": rep["peak_device_bytes"] / 1e9, "clocks": clocks}
+
+
+def run_ensemble(args):
+    """--workload ensemble: the batched ensemble alone as the bench line."""
+    from paper_2205_02774_gb300 import build
+    build()
+    e = ensemble_run(args.members, args.steps, args.warmup, args.storage)
+    line = {"metric": "MLUPS", "value": e["value"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": e["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": e["workload"], "storage": args.storage, "cells": e["cells"],
+                       "members": e["members"], "block_steps": e["block_steps"], "tile": e["tile"],
+                       "l2": "inputs larger than L2", "setup_s": e["setup_s"]},
+            "roofline": e["roofline"], "failed_members": e["failed_members"], "clocks": e["clocks"],
+            "gpu_launches": e["gpu_launches"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """--workload serve: the served stream alone as the bench line."""
+    from paper_2205_02774_gb300 import build
+    build()
+    s = serve_run(args.jobs, args.serve_steps_scale)
+    line = {"metric": "jobs/s", "value": s["value"], "unit": "jobs/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": s["workload"], "arrival_rate_per_s": 2.0,
+                       "steps_scale": args.serve_steps_scale, "hbm_budget_gb": 150}}
+    line.update({k: v for k, v in s.items() if k not in ("workload", "value", "unit")})
     print(json.dumps(line), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="channel_768x128x192")
-    ap.add_argument("--storage", choices=["fp32", "fp16s"], default="fp32")
-    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--workload", default="channel_1536x256x384")
+    ap.add_argument("--storage", choices=["fp32", "fp16s"], default="fp16s")
+    ap.add_argument("--cpu-steps", type=int, default=4, help="cpu_baseline: oracle steps on the sample")
+    ap.add_argument("--cpu-cells", type=float, default=1.5e8,
+                    help="cpu_baseline: cell updates of the sample (a slice with fewer wall-normal rows)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="", help="launch tile 'layout,zc,wall_zc' instead of the autotuner's")
-    ap.add_argument("--no-companion", action="store_true", help="skip the FP16-storage companion run")
+    ap.add_argument("--no-companion", action="store_true", help="skip the other storage form's companion run")
+    ap.add_argument("--no-extras", action="store_true", help="skip the ensemble and served-stream sub-objects")
     ap.add_argument("--collision", choices=["regularized", "bgk"], default="regularized",
                     help="bulk collision: regularized BGK (default) or plain BGK")
     ap.add_argument("--probes", type=int, default=0,
                     help="time the steps through step_probed with this many velocity probes (seeded random cells)")
     ap.add_argument("--sponge", action="store_true",
                     help="sponge zone of 0.4 delta before the outlet (K = 1000, p = 3, as in the paper's channel)")
-    ap.add_argument("--members", type=int, default=64, help="ensemble workload: channels in the batch")
-    ap.add_argument("--jobs", type=int, default=60, help="serve workload: jobs in the stream")
-    ap.add_argument("--steps-scale", type=float, default=0.1, help="serve workload: scale of the step counts")
+    ap.add_argument("--members", type=int, default=64, help="ensemble: channels in the batch")
+    ap.add_argument("--ensemble-steps", type=int, default=1000, help="ensemble sub-object: timed steps")
+    ap.add_argument("--jobs", type=int, default=100, help="served stream: jobs")
+    ap.add_argument("--serve-steps-scale", type=float, default=0.25, help="served stream: scale of the step counts")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

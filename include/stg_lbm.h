@@ -184,6 +184,15 @@ int stg_lbm_step_timed(stg_lbm *h, int64_t n, double *ms_step, double *ms_inlet)
  * wait expires, STG_ERR_UNSTABLE if a check failed. */
 int stg_lbm_stats(stg_lbm *h, stg_stats *out);
 
+/* Restart the running statistics (the FP64 sums of u and u u behind eqs.
+ * y_plus and v_rms, Sec. V) at the current step, e.g. to leave the inflow's
+ * start-up transient out of the time averages: waits for the handle's stream,
+ * zeroes the sums and makes the current step the origin of the sample count.
+ * The populations, the step counter and the inlet filter are untouched.
+ * Errors: STG_ERR_INVALID (NULL, a lattice in a batch), STG_ERR_TIMEOUT,
+ * STG_ERR_CUDA. */
+int stg_lbm_reset_stats(stg_lbm *h);
+
 /* Copy the populations (storage format g_i = f_i - w_i, 19*nx*ny*nz elements
  * of 4 or 2 bytes, layout f[i][z][y][x]) to or from host memory owned by the
  * caller; both wait for the handle's stream.  set_state also sets the step
@@ -413,6 +422,10 @@ const char *stg_lbm_version(void);
  * and each call clears the counter it needs before launching.  The first call
  * on a device (with that device current) looks up the scratch address with
  * cudaGetSymbolAddress: make that first call before any stream capture.
+ * Every later call made outside stream capture looks the address up again, so
+ * a device reset (cudaDeviceReset, which invalidates the array's old address)
+ * is picked up by the next such call; a call made during stream capture uses
+ * the address found by the last call outside capture on that device.
  * At most 2^31-1 cells; larger sizes, NULL pointers or a bad storage code
  * return STG_ERR_INVALID, CUDA failures STG_ERR_CUDA (message via
  * stg_lbm_last_error(NULL)).  Asynchronous: returns after enqueueing. */

@@ -96,6 +96,7 @@ _SIGNATURES = {
     "stg_lbm_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "stg_lbm_step_timed": (C.c_int, [C.c_void_p, C.c_int64, c_double_p, c_double_p]),
     "stg_lbm_stats": (C.c_int, [C.c_void_p, C.POINTER(stg_stats)]),
+    "stg_lbm_reset_stats": (C.c_int, [C.c_void_p]),
     "stg_lbm_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "stg_lbm_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int64]),
     "stg_lbm_get_inlet": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
@@ -192,6 +193,10 @@ def stg_lbm_stats(h, mean_sum=None, rey_sum=None):
     s.rey_sum = rey_sum.ctypes.data_as(c_double_p) if rey_sum is not None else None
     rc = lib().stg_lbm_stats(h, C.byref(s))
     return rc, s
+
+
+def stg_lbm_reset_stats(h):
+    return _check(lib().stg_lbm_reset_stats(h), h)
 
 
 def stg_lbm_get_state(h, out):

@@ -205,6 +205,10 @@ class Channel:
         return dict(rc=rc, step=s.step, n_samples=s.n_samples, mass=s.mass, mass0=s.mass0, mean_sum=m,
                     rey_sum=r, error=A.stg_lbm_last_error(self.h) if rc else "")
 
+    def reset_stats(self):
+        """Restart the running statistics at the current step."""
+        A.stg_lbm_reset_stats(self.h)
+
     def info(self):
         i = A.stg_lbm_info(self.h)
         return {k: getattr(i, k) for k, _ in A.stg_info._fields_}

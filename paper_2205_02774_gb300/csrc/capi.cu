@@ -890,6 +890,19 @@ int stg_lbm_stats(stg_lbm *h, stg_stats *out)
     return h->sticky;
 }
 
+int stg_lbm_reset_stats(stg_lbm *h)
+{
+    if (!h) return fail(nullptr, STG_ERR_INVALID, "handle is NULL");
+    if (h->batch) return fail(h, STG_ERR_INVALID, "the lattice is in a batch; remove it first");
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    const size_t m = (size_t)h->d.nx * h->d.ny;
+    CK(cudaMemsetAsync(h->stat_mean, 0, sizeof(double) * 3 * m, h->stream));
+    CK(cudaMemsetAsync(h->stat_rey, 0, sizeof(double) * 6 * m, h->stream));
+    h->t0_stats = h->t;
+    return wait_stream(h);
+}
+
 int stg_lbm_get_state(stg_lbm *h, void *host, size_t bytes)
 {
     if (!h || !host) return fail(h, STG_ERR_INVALID, "NULL argument");

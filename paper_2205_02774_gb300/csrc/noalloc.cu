@@ -60,12 +60,21 @@ extern "C" int stg_lattice_mass_noalloc(const void *pops, int32_t storage, int32
         stg::record_error("stg_lattice_mass_noalloc: device index beyond the supported 64");
         return STG_ERR_INVALID;
     }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) {
+        stg::record_error(std::string("stg_lattice_mass_noalloc: ") + cudaGetErrorString(e));
+        return STG_ERR_CUDA;
+    }
     NoAllocScratch *scratch = nullptr;
     {
-        // one-time set-up per device (with that device current): the device
-        // address of the scratch array; host code may not use its name directly
+        // set-up per device (with that device current): the device address of
+        // the scratch array (host code may not use its name directly).  Looked
+        // up on the first call and again on every call outside stream capture,
+        // so that an address invalidated by a device reset is replaced.
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_ptr[dev]) {
+        if (!g_scratch_ptr[dev] || cap == cudaStreamCaptureStatusNone) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess) {
@@ -76,7 +85,6 @@ extern "C" int stg_lattice_mass_noalloc(const void *pops, int32_t storage, int32
         }
         scratch = g_scratch_ptr[dev];
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the completion counter must start at zero (the kernel leaves it at zero)
     e = cudaMemsetAsync(&scratch->counter, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) {

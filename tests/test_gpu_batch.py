@@ -170,3 +170,60 @@ def test_admission_estimate_bounds_the_allocation(kw):
     used = g.info()["device_bytes"]
     g.close()
     assert used <= est <= 1.5 * used + 4e6
+
+
+def _oracle_200():
+    import oracle as O
+    c = SMALL  # 64x32x32, 100 modes, statistics every 10 steps
+    o = O.Sim.from_case(c)
+    o.step(200)
+    m, r, n = o.stats()
+    return o.pops(), m, r, n
+
+
+def _fluct(mean_sum, rey_sum, n, nz):
+    cnt = n * nz
+    return rey_sum[0] / cnt - (mean_sum[0] / cnt) ** 2
+
+
+def test_batch_and_served_members_match_oracle():
+    """Batched and served forms against the FP64 oracle: the 64x32x32 channel
+    run for 200 steps as a member of a batch (beside members of other sizes and
+    an FP16 copy of itself) and as a job of the serving loop (beside other
+    jobs) gives the oracle's velocity and statistics, FP32 storage at 1e-4
+    normwise (the single-channel parity bound), FP16 storage at 1e-2."""
+    from paper_2205_02774_gb300.channel import Channel
+    from paper_2205_02774_gb300.serving import Batch, serve
+    from gpu_helpers import velocity, normwise
+    fo, mo, ro, no = _oracle_200()
+    c = SMALL
+    chans = [Channel.from_case(c, check_every=20, mass_tol=0.1),
+             Channel.from_case(c.with_(storage="fp16s"), check_every=20, mass_tol=0.1),
+             Channel.from_case(_cases()[0], check_every=6, mass_tol=0.5),
+             Channel.from_case(_cases()[1], check_every=6, mass_tol=0.5)]
+    b = Batch()
+    for ch in chans:
+        b.add(ch)
+    b.step(200)
+    errs = {}
+    for name, ch, tol in (("fp32", chans[0], 1e-4), ("fp16s", chans[1], 1e-2)):
+        st = ch.stats()
+        assert st["rc"] == 0, st["error"]
+        assert st["n_samples"] == no == 20
+        errs[name] = (normwise(velocity(ch.populations()), velocity(fo)), normwise(st["mean_sum"], mo),
+                      normwise(st["rey_sum"], ro),
+                      normwise(_fluct(st["mean_sum"], st["rey_sum"], no, c.nz), _fluct(mo, ro, no, c.nz)))
+        assert max(errs[name][:3]) < tol, (name, errs[name])
+        assert errs[name][3] < (1e-2 if name == "fp32" else 5e-2), (name, errs[name])
+    b.close()
+    for ch in chans:
+        ch.close()
+    # the same channel as a served job among others arriving at the same time
+    jobs = [Job(0.0, SMALL, 200)] + _jobs()[:3]
+    results, rep = serve(jobs, hbm_budget_bytes=8e9, check_every=20, keep_stats=True)
+    assert rep["completed"] == len(jobs)
+    r0 = results[0]
+    assert r0["status"] == 0 and r0["n_samples"] == no
+    errs["served"] = (normwise(r0["mean_sum"], mo), normwise(r0["rey_sum"], ro))
+    assert max(errs["served"]) < 1e-4, errs
+    print("batched / served vs oracle", errs)
