@@ -4,15 +4,17 @@ One step = the STG inlet kernel plus the fused stream/collide pass over the
 whole lattice (FP64 statistics every 10 steps, FP64 mass check every 100),
 i.e. one pass of the whole hot path.  Default workload: the refined Re_tau =
 180 channel on a 1536x256x384 D3Q19 lattice (h = 128, 151M cells, 200 STG
-modes) with populations stored as shifted FP16 (f - w_i, FP32 arithmetic),
-inputs resident in HBM, lattice (5.7 GB) far larger than L2.  The same line
-carries the FP32-storage companion on the same lattice, the end-to-end figure
-through the public API, the CPU oracle on a bounded sample, and two
-sub-objects: the batched ensemble (64 channels) and the served job stream
-(Poisson arrivals, continuous batching, p50/p99 latency).
+modes) with populations stored as shifted FP16 (f - w_i) written by
+stochastic rounding (FP32 arithmetic), two lattices, inputs resident in HBM,
+lattice (5.7 GB) far larger than L2.  The same line carries companions on
+the same lattice (round-to-nearest FP16, FP32, and the one-lattice in-place
+update), the end-to-end figure through the public API, the CPU oracle on a
+bounded sample, and two sub-objects: the batched ensemble (64 channels) and
+the served job stream (Poisson arrivals, continuous batching, p50/p99
+latency).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --storage fp32 --workload channel_768x128x192 --no-extras
+  python bench.py --storage fp32 --streaming aa --workload channel_768x128x192 --no-extras
   python bench.py --workload ensemble [--members 64] [--steps K]   (batched ensemble alone)
   python bench.py --workload serve [--jobs 100] [--serve-steps-scale 0.25]   (served stream alone)
 
@@ -38,7 +40,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_CELL = {"fp32": 152, "fp16s": 76}  # 19 populations read + 19 written
+BYTES_PER_CELL = {"fp32": 152, "fp16s": 76, "fp16sr": 76}  # 19 populations read + 19 written
 
 
 def _peaks():
@@ -55,7 +57,7 @@ def _kernel_hash():
     """Hash of the step kernels' source with comments and white space removed
     (a comment edit does not change the kernel whose counters were taken)."""
     h = hashlib.sha256()
-    for f in ("step_kernel.cu", "d3q19.cuh", "internal.h", "lbm_cell.cuh", "reduce.cuh"):
+    for f in ("step_kernel.cu", "step_kernel.cuh", "d3q19.cuh", "internal.h", "lbm_cell.cuh", "reduce.cuh"):
         with open(os.path.join(ROOT, "paper_2205_02774_gb300", "csrc", f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
@@ -64,10 +66,11 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(workload, storage):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"lbm_step_kernel_{workload}_{storage}.md")
+def _traffic(workload, storage, streaming="pull"):
+    """DRAM bytes of one step pass from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    tag = storage if streaming == "pull" else f"{storage}_{streaming}"
+    path = os.path.join(ROOT, "profiles", f"lbm_step_kernel_{workload}_{tag}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -348,12 +351,14 @@ def measure_channel(c, args, rank=0, dist=None, seed=None, sample_clocks=True):
         raise RuntimeError(f"channel check failed: {st['error']}")
     # dominant kernel: device time of one step pass (the two step launches)
     ms_step, ms_inlet = ch.step_timed(min(200, max(20, args.steps // 10)))
+    device_gb = ch.info()["device_bytes"] / 1e9
     ch.close()
     del ch
     torch.cuda.synchronize()
     bpc = BYTES_PER_CELL[c.storage]
     peak, _ = _peaks()
     return {"value": value, "ms": ms, "ms_per_step": ms / args.steps, "tile": list(tile), "clocks": clocks,
+            "device_gb": device_gb,
             "ms_step": ms_step, "ms_inlet": ms_inlet,
             "hbm_frac_of_step": bpc * c.cells * args.steps / (ms * 1e-3) / 1e9 / peak}
 
@@ -396,7 +401,7 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    c = _variant(case(args.workload).with_(storage=args.storage), args)
+    c = _variant(case(args.workload).with_(storage=args.storage, streaming=args.streaming), args)
     m = measure_channel(c, args, rank, dist, seed=rank_seed(c.seed, rank))
     if dist is not None:
         dist.barrier()
@@ -406,17 +411,17 @@ def run_ours(args):
 
     # the committed counters were taken on the default variant
     plain = args.collision == "regularized" and not args.sponge and args.probes == 0
-    traffic = _traffic(args.workload, c.storage) if plain else None
+    traffic = _traffic(args.workload, c.storage, c.streaming) if plain else None
     line = {
         "metric": "MLUPS", "value": m["value"], "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "storage": c.storage, "cells": c.cells, "lattice": "D3Q19",
-                   "arithmetic": "fp32", "tile": m["tile"],
+        "config": {"workload": args.workload, "storage": c.storage, "streaming": c.streaming, "cells": c.cells,
+                   "lattice": "D3Q19", "arithmetic": "fp32", "tile": m["tile"], "device_gb": m["device_gb"],
                    "collision": c.collision, "sponge_len": c.sponge_len, "probes": args.probes,
                    "stg_modes": c.n_modes,
                    "stats_every": c.stats_every,
-                   "l2": "inputs larger than L2 (lattice %.2f GB)" % (2 * 19 * c.cells * BYTES_PER_CELL[c.storage] / 38 / 1e9),
+                   "l2": "inputs larger than L2 (lattice %.2f GB)" % (19 * c.cells * BYTES_PER_CELL[c.storage] / 38 / 1e9),
                    "parallelism": f"replicas x{ws}"},
         "roofline": roofline(BYTES_PER_CELL[c.storage], c.cells, m["ms_step"], m["ms_inlet"], traffic, STEP_KERNEL),
         "hbm_frac_of_step": m["hbm_frac_of_step"],
@@ -425,16 +430,23 @@ def run_ours(args):
     }
     line["e2e"] = end_to_end(c, args.steps)
     if not args.no_companion:
-        # the same channel in the other storage form, timed the same way
-        other = "fp32" if c.storage == "fp16s" else "fp16s"
-        c2 = c.with_(storage=other)
-        m2 = measure_channel(c2, args)
-        t2 = _traffic(args.workload, other) if plain else None
-        line[f"{other}_companion"] = {
-            "storage": other, "value": m2["value"], "unit": "MLUPS", "ms_per_step": m2["ms_per_step"],
-            "hbm_frac_of_step": m2["hbm_frac_of_step"], "tile": m2["tile"], "clocks": m2["clocks"],
-            "roofline": roofline(BYTES_PER_CELL[other], c2.cells, m2["ms_step"], m2["ms_inlet"], t2, STEP_KERNEL),
-            "gpu_launches": _launches(c2, args.warmup, args.steps)}
+        # the same channel in the other storage forms and streaming scheme, timed the same way
+        comps = []
+        for st in ("fp16sr", "fp16s", "fp32"):
+            if st != c.storage:
+                comps.append((st, c.streaming))
+        comps.append((c.storage, "aa" if c.streaming == "pull" else "pull"))
+        line["companions"] = []
+        for st, sm in comps:
+            c2 = c.with_(storage=st, streaming=sm)
+            m2 = measure_channel(c2, args)
+            t2 = _traffic(args.workload, st, sm) if plain else None
+            line["companions"].append({
+                "storage": st, "streaming": sm, "value": m2["value"], "unit": "MLUPS",
+                "ms_per_step": m2["ms_per_step"], "hbm_frac_of_step": m2["hbm_frac_of_step"], "tile": m2["tile"],
+                "clocks": m2["clocks"], "device_gb": m2["device_gb"],
+                "roofline": roofline(BYTES_PER_CELL[st], c2.cells, m2["ms_step"], m2["ms_inlet"], t2, STEP_KERNEL),
+                "gpu_launches": _launches(c2, args.warmup, args.steps)})
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, c.storage, args.cpu_steps, args.cpu_cells,
                                             extra=dict(collision=c.collision, sponge_len=c.sponge_len,
@@ -561,13 +573,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="channel_1536x256x384")
-    ap.add_argument("--storage", choices=["fp32", "fp16s"], default="fp16s")
+    ap.add_argument("--storage", choices=["fp32", "fp16s", "fp16sr"], default="fp16sr",
+                    help="population storage: FP32, shifted binary16 rounded to nearest, or by stochastic rounding")
+    ap.add_argument("--streaming", choices=["pull", "aa"], default="pull",
+                    help="two lattices (pull) or one lattice updated in place (AA pattern)")
     ap.add_argument("--cpu-steps", type=int, default=4, help="cpu_baseline: oracle steps on the sample")
     ap.add_argument("--cpu-cells", type=float, default=1.5e8,
                     help="cpu_baseline: cell updates of the sample (a slice with fewer wall-normal rows)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default="", help="launch tile 'layout,zc,wall_zc' instead of the autotuner's")
-    ap.add_argument("--no-companion", action="store_true", help="skip the other storage form's companion run")
+    ap.add_argument("--no-companion", action="store_true",
+                    help="skip the companion runs (other storage forms, other streaming scheme)")
     ap.add_argument("--no-extras", action="store_true", help="skip the ensemble and served-stream sub-objects")
     ap.add_argument("--collision", choices=["regularized", "bgk"], default="regularized",
                     help="bulk collision: regularized BGK (default) or plain BGK")

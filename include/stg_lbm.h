@@ -57,7 +57,10 @@ extern "C" {
 
 /* stg_domain.storage */
 #define STG_FP32 0
-#define STG_FP16_SHIFTED 1
+#define STG_FP16_SHIFTED 1     /* binary16 of f_i - w_i, round to nearest even */
+#define STG_FP16_SHIFTED_SR 2  /* binary16 of f_i - w_i, stochastic rounding (unbiased: updates
+                                * smaller than half a binary16 spacing are kept on average; the
+                                * random bits are a fixed function of cell, step and population) */
 /* stg_domain.collision */
 #define STG_REGULARIZED 0   /* BGK relaxation of the regularized non-equilibrium part */
 #define STG_BGK 1           /* plain BGK, eq. (lbe) */
@@ -69,17 +72,25 @@ extern "C" {
 /* stg_domain.bc_y */
 #define STG_BC_Y_WALLS 0    /* half-way bounce-back at y = -1/2 and y = ny - 1/2 */
 #define STG_BC_Y_PERIODIC 1
+/* stg_domain.streaming: how the pull of eq. (lbe), f_i(x) <- f*_i(x - c_i), is laid out in memory.
+ * Both give the same populations, statistics and mass; they differ in memory and in layout. */
+#define STG_STREAM_PULL 0   /* two lattices: each step reads the previous one and writes the next
+                             * (2 x 19 populations per cell) */
+#define STG_STREAM_AA 1     /* one lattice updated in place (AA pattern, 19 populations per cell):
+                             * steps of even index read slot opp(i) of cell x - c_i and write slot i
+                             * of cell x + c_i, steps of odd index read slot i and write slot opp(i)
+                             * of the same cell.  Needs an even nx >= 4 and 19 nx ny nz < 2^32. */
 
 /* Lattice, physics and cadence of one channel.  z is always periodic. */
 typedef struct {
     int32_t nx, ny, nz;   /* lattice size; nx >= 3 with the inlet/outlet */
-    int32_t storage;      /* STG_FP32 | STG_FP16_SHIFTED */
+    int32_t storage;      /* STG_FP32 | STG_FP16_SHIFTED | STG_FP16_SHIFTED_SR */
     int32_t collision;    /* STG_REGULARIZED | STG_BGK */
     int32_t bc_x;         /* STG_BC_X_* */
     int32_t bc_y;         /* STG_BC_Y_* */
     int32_t stats_every;  /* accumulate u and u u over z and time after every k-th step; 0 = off */
     int32_t check_every;  /* FP64 mass / NaN check after every k-th step; 0 = off */
-    int32_t pad0;
+    int32_t streaming;    /* STG_STREAM_PULL (0) | STG_STREAM_AA */
     double tau0;          /* molecular relaxation time, nu0 = (tau0 - 1/2)/3, eq. (lbe-nu) */
     double c_smag;        /* C in nu_t = C delta^2 |S| (C = Cs^2), eq. (smogrinsky_model) */
     double force[3];      /* body-force density, Guo forcing, eq. (bodyforce) */

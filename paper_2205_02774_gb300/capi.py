@@ -15,10 +15,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libstglbm.so")
 
 STG_OK, STG_ERR_INVALID, STG_ERR_NOMEM, STG_ERR_UNSTABLE, STG_ERR_TIMEOUT, STG_ERR_CUDA = range(6)
-STG_FP32, STG_FP16_SHIFTED = 0, 1
+STG_FP32, STG_FP16_SHIFTED, STG_FP16_SHIFTED_SR = 0, 1, 2
 STG_REGULARIZED, STG_BGK = 0, 1
 STG_BC_X_INLET_OUTLET, STG_BC_X_PERIODIC = 0, 1
 STG_BC_Y_WALLS, STG_BC_Y_PERIODIC = 0, 1
+STG_STREAM_PULL, STG_STREAM_AA = 0, 1
 
 c_double_p = C.POINTER(C.c_double)
 
@@ -26,7 +27,7 @@ c_double_p = C.POINTER(C.c_double)
 class stg_domain(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("storage", C.c_int32),
                 ("collision", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32),
-                ("stats_every", C.c_int32), ("check_every", C.c_int32), ("pad0", C.c_int32),
+                ("stats_every", C.c_int32), ("check_every", C.c_int32), ("streaming", C.c_int32),
                 ("tau0", C.c_double), ("c_smag", C.c_double), ("force", C.c_double * 3),
                 ("mass_tol", C.c_double), ("sponge_len", C.c_double), ("sponge_K", C.c_double),
                 ("sponge_p", C.c_double)]

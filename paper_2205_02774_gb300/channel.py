@@ -38,11 +38,12 @@ class _TorchAllocator:
 
 
 def _domain(nx, ny, nz, storage, collision, bc_x, bc_y, stats_every, check_every, tau0, c_smag, force,
-            mass_tol, sponge=(0.0, 1000.0, 3.0)):
+            mass_tol, sponge=(0.0, 1000.0, 3.0), streaming="pull"):
     d = A.stg_domain()
+    d.streaming = {"pull": A.STG_STREAM_PULL, "aa": A.STG_STREAM_AA}[streaming]
     d.sponge_len, d.sponge_K, d.sponge_p = sponge
     d.nx, d.ny, d.nz = nx, ny, nz
-    d.storage = {"fp32": A.STG_FP32, "fp16s": A.STG_FP16_SHIFTED}[storage]
+    d.storage = {"fp32": A.STG_FP32, "fp16s": A.STG_FP16_SHIFTED, "fp16sr": A.STG_FP16_SHIFTED_SR}[storage]
     d.collision = {"regularized": A.STG_REGULARIZED, "bgk": A.STG_BGK}[collision]
     d.bc_x = {"stg": A.STG_BC_X_INLET_OUTLET, "periodic": A.STG_BC_X_PERIODIC}[bc_x]
     d.bc_y = {"walls": A.STG_BC_Y_WALLS, "periodic": A.STG_BC_Y_PERIODIC}[bc_y]
@@ -55,12 +56,14 @@ def _domain(nx, ny, nz, storage, collision, bc_x, bc_y, stats_every, check_every
 
 def create_structs(nx, ny, nz, *, profile=None, tau0=0.52, c_smag=0.01, force=(0.0, 0.0, 0.0), storage="fp32",
                    collision="regularized", bc_x="stg", bc_y="walls", stats_every=0, check_every=0, mass_tol=0.0,
-                   n_modes=100, C_l=3.0, alpha=0.01, t_filter=0.0, mach_target=0.0516, sponge=(0.0, 1000.0, 3.0)):
+                   n_modes=100, C_l=3.0, alpha=0.01, t_filter=0.0, mach_target=0.0516, sponge=(0.0, 1000.0, 3.0),
+                   streaming="pull"):
     """The stg_domain, stg_rans_profile and stg_params of a lattice (the last
     two None for periodic x), plus the arrays they point into (keep them
-    alive while the structs are in use).  sponge = (length, K, p)."""
+    alive while the structs are in use).  sponge = (length, K, p);
+    streaming: "pull" (two lattices) or "aa" (one lattice in place)."""
     domain = _domain(nx, ny, nz, storage, collision, bc_x, bc_y, stats_every, check_every, tau0, c_smag, force,
-                     mass_tol, sponge)
+                     mass_tol, sponge, streaming)
     keep = []
     rans = None
     params = None
@@ -83,7 +86,8 @@ def case_kwargs(case):
     return dict(profile=case.profile() if case.bc_x == "stg" else None, tau0=case.tau0, c_smag=case.c_smag,
                 force=case.force, storage=case.storage, collision=case.collision, bc_x=case.bc_x, bc_y=case.bc_y,
                 stats_every=case.stats_every, n_modes=case.n_modes, t_filter=case.t_filter,
-                mach_target=case.mach_target, sponge=(case.sponge_len, case.sponge_K, case.sponge_p))
+                mach_target=case.mach_target, sponge=(case.sponge_len, case.sponge_K, case.sponge_p),
+                streaming=case.streaming)
 
 
 class Channel:
@@ -95,7 +99,8 @@ class Channel:
     def __init__(self, nx, ny, nz, *, profile=None, tau0=0.52, c_smag=0.01, force=(0.0, 0.0, 0.0),
                  storage="fp32", collision="regularized", bc_x="stg", bc_y="walls", stats_every=0,
                  check_every=0, mass_tol=0.0, n_modes=100, C_l=3.0, alpha=0.01, t_filter=0.0,
-                 mach_target=0.0516, seed=0, stream=None, use_torch_allocator=True, sponge=(0.0, 1000.0, 3.0)):
+                 mach_target=0.0516, seed=0, stream=None, use_torch_allocator=True, sponge=(0.0, 1000.0, 3.0),
+                 streaming="pull"):
         import torch
         self.torch = torch
         self.nx, self.ny, self.nz = nx, ny, nz
@@ -106,7 +111,7 @@ class Channel:
             nx, ny, nz, profile=profile, tau0=tau0, c_smag=c_smag, force=force, storage=storage,
             collision=collision, bc_x=bc_x, bc_y=bc_y, stats_every=stats_every, check_every=check_every,
             mass_tol=mass_tol, n_modes=n_modes, C_l=C_l, alpha=alpha, t_filter=t_filter, mach_target=mach_target,
-            sponge=sponge)
+            sponge=sponge, streaming=streaming)
         self._allocator = _TorchAllocator(torch, self.device, self.stream) if use_torch_allocator else None
         self.h = A.stg_lbm_create(self.domain, rans, params, seed,
                                   self._allocator.struct if self._allocator else None, self.stream.cuda_stream)

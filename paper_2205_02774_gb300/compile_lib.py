@@ -16,7 +16,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstglbm.so")
-SOURCES = ["capi.cu", "step_kernel.cu", "inlet_kernel.cu", "noalloc.cu", "batch.cu", "serve.cu", "probe.cu"]
+STEP_TUS = ["step_f32_reg.cu", "step_f32_bgk.cu", "step_f16_reg.cu", "step_f16_bgk.cu", "step_f16sr_reg.cu",
+            "step_f16sr_bgk.cu"]
+SOURCES = ["capi.cu", "step_kernel.cu", *STEP_TUS, "inlet_kernel.cu", "noalloc.cu", "batch.cu", "serve.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE,
               "--expt-relaxed-constexpr"]
@@ -24,7 +26,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSR
 # root (a few ulp, far inside the parity tolerance) and flushes denormals; the
 # FP64 setup code is unaffected by these flags.
 FAST_FP32 = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
-FAST_TUS = {"step_kernel.cu"}
+FAST_TUS = {"step_kernel.cu", *STEP_TUS}
 
 
 def _nvcc():

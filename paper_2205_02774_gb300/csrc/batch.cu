@@ -415,6 +415,13 @@ int stg_batch_autotune(stg_batch *b, int32_t trial_passes, stg_tile *chosen)
     const stg_tile *cand = tile_candidates(&ncand);
     int rc = order_after_members(b);
     if (rc) return rc;
+    // in-place members: their trial passes update the lattice, saved first and put back
+    std::vector<std::vector<unsigned char>> keep(b->m.size());
+    std::vector<stg::StepCtl> keep_ctl(b->m.size());
+    for (size_t d = 0; d < b->m.size(); ++d) {
+        rc = save_trial_state(b->m[d], keep[d], keep_ctl[d]);
+        if (rc) return bfail(b, rc, "member " + std::to_string(d) + ": " + b->m[d]->err);
+    }
     stg_tile best = b->m[0]->tile;
     float best_ms = -1.f;
     for (int c = 0; c < ncand; ++c) {
@@ -425,7 +432,7 @@ int stg_batch_autotune(stg_batch *b, int32_t trial_passes, stg_tile *chosen)
             BCK(cudaEventRecord(b->fork, b->stream));
             for (size_t d = 0; d < b->m.size(); ++d) {
                 BCK(cudaStreamWaitEvent(b->ms[d], b->fork, 0));
-                BCK(trial_pass(b->m[d], cand[c], b->ms[d]));
+                BCK(trial_pass(b->m[d], cand[c], b->ms[d], k));
                 BCK(cudaEventRecord(b->join[d], b->ms[d]));
                 BCK(cudaStreamWaitEvent(b->stream, b->join[d], 0));
             }
@@ -441,6 +448,10 @@ int stg_batch_autotune(stg_batch *b, int32_t trial_passes, stg_tile *chosen)
     }
     rc = order_members_after(b);
     if (rc) return rc;
+    for (size_t d = 0; d < b->m.size(); ++d) {
+        rc = restore_trial_state(b->m[d], keep[d], keep_ctl[d]);
+        if (rc) return bfail(b, rc, "member " + std::to_string(d) + ": " + b->m[d]->err);
+    }
     for (size_t d = 0; d < b->m.size(); ++d) {
         rc = apply_tile(b->m[d], best);
         if (rc) return bfail(b, rc, "member " + std::to_string(d) + ": " + b->m[d]->err);

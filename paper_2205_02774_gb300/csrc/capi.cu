@@ -13,6 +13,7 @@
 #include <utility>
 #include <vector>
 
+#include "aa_layout.cuh"
 #include "d3q19.cuh"
 #include "handle.h"
 
@@ -293,6 +294,21 @@ float *ubc_plane(const stg_lbm *h, int parity)
     return h->ubc + (size_t)(parity & 1) * 3 * (size_t)h->d.ny * h->d.nz;
 }
 
+// where the populations of the current state live (for probes and block reads)
+stg::LatticeView lattice_view(const stg_lbm *h)
+{
+    stg::LatticeView v{};
+    v.nx = h->d.nx;
+    v.ny = h->d.ny;
+    v.nz = h->d.nz;
+    v.bc_x = h->d.bc_x;
+    v.bc_y = h->d.bc_y;
+    v.aa = h->aa ? 1 : 0;
+    v.P = h->P;
+    v.t = h->t;
+    return v;
+}
+
 stg::StepArgs step_args(const stg_lbm *h, int parity)
 {
     stg::StepArgs a{};
@@ -325,6 +341,7 @@ stg::StepArgs step_args(const stg_lbm *h, int parity)
     a.parity = parity;
     a.stats_every = h->d.stats_every;
     a.interior = h->interior;
+    a.aa = h->aa ? 1 : 0;
     a.tile_layout = h->tile.interior_layout;
     a.tile_zc = h->tile.interior_zc;
     a.tile_wall_zc = h->tile.wall_zc;
@@ -527,6 +544,50 @@ int queue_check_readback(stg_lbm *h, int64_t t_before)
 
 namespace {
 
+// Rows of an in-place lattice after t completed steps to or from the
+// canonical arrangement (f*_i(x) in slot i of cell x; aa_layout.cuh): plane
+// swap for even t, shifted rows for odd t.  T is the element type (4 or 2
+// bytes, copied bit for bit).
+template <typename T>
+void aa_convert(const stg_lbm *h, int64_t t, const T *src, T *dst, bool to_canonical)
+{
+    const int nx = h->d.nx, ny = h->d.ny, nz = h->d.nz;
+    const size_t P = h->P;
+    const bool px = h->d.bc_x == STG_BC_X_PERIODIC, py = h->d.bc_y == STG_BC_Y_PERIODIC;
+    for (int i = 0; i < 19; ++i) {
+        const int o = stg::opp_of(i), cx = stg::cx_of(i), cy = stg::cy_of(i), cz = stg::cz_of(i);
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y) {
+                const size_t row = ((size_t)z * ny + y) * nx;
+                // canonical row (i, y, z) and the stored slots its elements map to
+                auto canon = [&](int x) -> size_t { return (size_t)i * P + row + x; };
+                auto own = [&](int x) -> size_t { return (size_t)o * P + row + x; };
+                auto move = [&](size_t c, size_t s) {
+                    if (to_canonical) dst[c] = src[s];
+                    else dst[s] = src[c];
+                };
+                if ((t & 1) == 0) {
+                    for (int x = 0; x < nx; ++x) move(canon(x), own(x));
+                    continue;
+                }
+                int yt = y + cy, zt = z + cz;
+                zt = zt < 0 ? zt + nz : (zt >= nz ? zt - nz : zt);
+                if (py) yt = yt < 0 ? yt + ny : (yt >= ny ? yt - ny : yt);
+                if (yt < 0 || yt >= ny) {
+                    for (int x = 0; x < nx; ++x) move(canon(x), own(x));
+                    continue;
+                }
+                const size_t trow = (size_t)i * P + ((size_t)zt * ny + yt) * nx;
+                for (int x = 0; x < nx; ++x) {
+                    int xt = x + cx;
+                    if (px) xt = xt < 0 ? xt + nx : (xt >= nx ? xt - nx : xt);
+                    if (xt < 0 || xt >= nx) move(canon(x), own(x));
+                    else move(canon(x), trow + xt);
+                }
+            }
+    }
+}
+
 int compute_mass(stg_lbm *h, double *out)
 {
     stg::MassArgs m{};
@@ -598,13 +659,17 @@ int validate(const stg_domain *d, const stg_rans_profile *r, const stg_params *p
     const double cells = (double)d->nx * d->ny * d->nz;
     if (cells > 2147483647.0) return fail(nullptr, STG_ERR_INVALID, "more than 2^31-1 cells");
     if (d->ny > 65535) return fail(nullptr, STG_ERR_INVALID, "ny must be <= 65535");
-    if (d->storage != STG_FP32 && d->storage != STG_FP16_SHIFTED) return fail(nullptr, STG_ERR_INVALID, "bad storage");
+    if (d->storage != STG_FP32 && d->storage != STG_FP16_SHIFTED && d->storage != STG_FP16_SHIFTED_SR)
+        return fail(nullptr, STG_ERR_INVALID, "bad storage");
     if (d->collision != STG_REGULARIZED && d->collision != STG_BGK) return fail(nullptr, STG_ERR_INVALID, "bad collision");
     if (d->bc_x != STG_BC_X_INLET_OUTLET && d->bc_x != STG_BC_X_PERIODIC) return fail(nullptr, STG_ERR_INVALID, "bad bc_x");
     if (d->bc_y != STG_BC_Y_WALLS && d->bc_y != STG_BC_Y_PERIODIC) return fail(nullptr, STG_ERR_INVALID, "bad bc_y");
     if (!(d->tau0 > 0.5) || !std::isfinite(d->tau0)) return fail(nullptr, STG_ERR_INVALID, "tau0 must be > 1/2");
     if (!(d->c_smag >= 0.0) || !std::isfinite(d->c_smag)) return fail(nullptr, STG_ERR_INVALID, "c_smag must be >= 0");
     if (d->stats_every < 0 || d->check_every < 0) return fail(nullptr, STG_ERR_INVALID, "negative cadence");
+    if (d->streaming != STG_STREAM_PULL && d->streaming != STG_STREAM_AA) return fail(nullptr, STG_ERR_INVALID, "bad streaming");
+    if (d->streaming == STG_STREAM_AA && (d->nx % 2 != 0 || d->nx < 4 || 19.0 * cells >= 4294967296.0))
+        return fail(nullptr, STG_ERR_INVALID, "in-place streaming needs an even nx >= 4 and 19 nx ny nz < 2^32");
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(d->force[a])) return fail(nullptr, STG_ERR_INVALID, "non-finite force");
     if (!(d->sponge_len >= 0.0) || !std::isfinite(d->sponge_len))
@@ -693,8 +758,9 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
     }
     h->P = (size_t)nx * ny * nz;
     h->elem = domain->storage == STG_FP32 ? 4 : 2;
+    h->aa = domain->streaming == STG_STREAM_AA;
     h->lat[0] = dalloc(h, 19 * h->P * h->elem);
-    h->lat[1] = dalloc(h, 19 * h->P * h->elem);
+    h->lat[1] = h->aa ? h->lat[0] : dalloc(h, 19 * h->P * h->elem);  // in place: one lattice
     h->ubc = (float *)dalloc(h, sizeof(float) * 6 * (size_t)ny * nz);
     h->uf = (float *)dalloc(h, sizeof(float) * 3 * (size_t)ny * nz);
     h->ctl = (StepCtl *)dalloc(h, sizeof(StepCtl));
@@ -746,8 +812,9 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
         rc = build_inlet(h, rans, seed);
         if (rc) return bail(rc);
     }
+    // in place, the state before a step of even index keeps f*_i in slot opp(i)
     e = stg::launch_init_equilibrium(h->lat[0], domain->storage, nx, ny, nz, h->inout ? h->u_int : nullptr,
-                                     h->stream);
+                                     h->aa ? 1 : 0, h->stream);
     if (e != cudaSuccess) {
         cuda_fail(h, e, "init kernel");
         return bail(STG_ERR_CUDA);
@@ -768,12 +835,14 @@ int stg_lbm_create(const stg_domain *domain, const stg_rans_profile *rans, const
 
 int stg_lbm_estimate_bytes(const stg_domain *d, const stg_params *p, int64_t *bytes)
 {
-    if (!d || !bytes || d->nx < 1 || d->ny < 1 || d->nz < 1 || (d->storage != STG_FP32 && d->storage != STG_FP16_SHIFTED))
+    if (!d || !bytes || d->nx < 1 || d->ny < 1 || d->nz < 1 ||
+        (d->storage != STG_FP32 && d->storage != STG_FP16_SHIFTED && d->storage != STG_FP16_SHIFTED_SR))
         return fail(nullptr, STG_ERR_INVALID, "estimate: bad domain");
     auto r = [](double b) { return (double)(((int64_t)std::max(b, 16.0) + 255) & ~int64_t(255)); };
     const double nx = d->nx, ny = d->ny, nz = d->nz, P = nx * ny * nz;
     const double elem = d->storage == STG_FP32 ? 4.0 : 2.0;
-    double b = 2 * r(19 * P * elem) + r(24 * ny * nz) + r(12 * ny * nz) + r(sizeof(StepCtl)) + r(24 * nx * ny) + r(48 * nx * ny) +
+    const double lattices = d->streaming == STG_STREAM_AA ? 1.0 : 2.0;
+    double b = lattices * r(19 * P * elem) + r(24 * ny * nz) + r(12 * ny * nz) + r(sizeof(StepCtl)) + r(24 * nx * ny) + r(48 * nx * ny) +
                r(8.0 * stg::step_grid_blocks(d->nx, d->ny, d->nz)) + 2 * r(16) + 2 * r(16) +
                r(8.0 * stg::mass_grid_blocks());
     if (d->sponge_len > 0.0) b += r(4 * nx);
@@ -909,7 +978,17 @@ int stg_lbm_get_state(stg_lbm *h, void *host, size_t bytes)
     if (bytes != 19 * h->P * h->elem) return fail(h, STG_ERR_INVALID, "state size mismatch");
     int rc = wait_stream(h);
     if (rc) return rc;
-    CK(cudaMemcpy(host, h->lat[h->t & 1], bytes, cudaMemcpyDeviceToHost));
+    if (!h->aa) {
+        CK(cudaMemcpy(host, h->lat[h->t & 1], bytes, cudaMemcpyDeviceToHost));
+        return STG_OK;
+    }
+    // in place: the stored arrangement depends on the step parity
+    std::vector<unsigned char> raw(bytes);
+    CK(cudaMemcpy(raw.data(), h->lat[0], bytes, cudaMemcpyDeviceToHost));
+    if (h->elem == 4)
+        aa_convert(h, h->t, reinterpret_cast<const uint32_t *>(raw.data()), static_cast<uint32_t *>(host), true);
+    else
+        aa_convert(h, h->t, reinterpret_cast<const uint16_t *>(raw.data()), static_cast<uint16_t *>(host), true);
     return STG_OK;
 }
 
@@ -921,7 +1000,16 @@ int stg_lbm_set_state(stg_lbm *h, const void *host, size_t bytes, int64_t step)
     if (step < 0) return fail(h, STG_ERR_INVALID, "negative step");
     int rc = wait_stream(h);
     if (rc) return rc;
-    CK(cudaMemcpy(h->lat[step & 1], host, bytes, cudaMemcpyHostToDevice));
+    if (!h->aa) {
+        CK(cudaMemcpy(h->lat[step & 1], host, bytes, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<unsigned char> raw(bytes);
+        if (h->elem == 4)
+            aa_convert(h, step, static_cast<const uint32_t *>(host), reinterpret_cast<uint32_t *>(raw.data()), false);
+        else
+            aa_convert(h, step, static_cast<const uint16_t *>(host), reinterpret_cast<uint16_t *>(raw.data()), false);
+        CK(cudaMemcpy(h->lat[0], raw.data(), bytes, cudaMemcpyHostToDevice));
+    }
     rc = reset_counters(h, step);
     if (rc) return rc;
     return compute_mass(h, &h->mass0);
@@ -939,7 +1027,8 @@ struct CkptHeader {
     int64_t t, t0_stats, t0_filter;
     double mass0;
     int64_t pop_bytes, uf_bytes, stat_bytes, plane_bytes;
-    int64_t reserved[5];
+    int64_t streaming;  // stg_domain.streaming of the lattice (0 in images without it)
+    int64_t reserved[4];
 };
 static_assert(sizeof(CkptHeader) == 128, "checkpoint header layout");
 constexpr char kCkptMagic[8] = {'S', 'T', 'G', 'C', 'K', 'P', 'T', '2'};
@@ -984,6 +1073,7 @@ int stg_lbm_save(stg_lbm *h, void *host, size_t bytes)
     hd.uf_bytes = (int64_t)(sizeof(float) * 3 * (size_t)h->d.ny * h->d.nz);
     hd.stat_bytes = (int64_t)(sizeof(double) * 9 * (size_t)h->d.nx * h->d.ny);
     hd.plane_bytes = hd.uf_bytes;
+    hd.streaming = h->d.streaming;  // the populations are stored in the lattice's own arrangement
     char *p = static_cast<char *>(host);
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
@@ -1009,7 +1099,7 @@ int stg_lbm_load(stg_lbm *h, const void *host, size_t bytes)
     std::memcpy(&hd, host, sizeof hd);
     if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.nx != h->d.nx || hd.ny != h->d.ny || hd.nz != h->d.nz ||
         hd.storage != h->d.storage || hd.t < 0 || hd.t0_stats < 0 || hd.t0_stats > hd.t || hd.t0_filter < 0 ||
-        hd.t0_filter > hd.t)
+        hd.t0_filter > hd.t || hd.streaming != h->d.streaming)
         return fail(h, STG_ERR_INVALID, "checkpoint does not match this lattice");
     int rc = wait_stream(h);
     if (rc) return rc;
@@ -1043,6 +1133,19 @@ int stg_lbm_get_block(stg_lbm *h, int32_t x0, int32_t y0, int32_t z0, int32_t bx
         return fail(h, STG_ERR_INVALID, "block outside the lattice");
     int rc = wait_stream(h);
     if (rc) return rc;
+    if (h->aa) {
+        // in place: gather the canonical populations on the device, then one copy
+        const size_t bytes = (size_t)19 * bx * by * bz * h->elem;
+        void *tmp = nullptr;
+        CK(cudaMalloc(&tmp, bytes));
+        cudaError_t e = stg::launch_gather_block(h->lat[0], h->d.storage, lattice_view(h), x0, y0, z0, bx, by, bz, tmp,
+                                                 h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(tmp);
+        if (e != cudaSuccess) return cuda_fail(h, e, "in-place block gather");
+        return STG_OK;
+    }
     // one 3-D copy per population: rows of bx elements
     for (int i = 0; i < 19; ++i) {
         cudaMemcpy3DParms m{};
@@ -1133,7 +1236,7 @@ int stg_lbm_step_probed(stg_lbm *h, int64_t n, float *u_host)
     for (int64_t s = 0; s < n; ++s) {
         CK(cudaGraphLaunch(h->g_single[h->t & 1][is_stats_step(h, h->t) ? 1 : 0], h->stream));
         h->t += 1;
-        CK(stg::launch_probe(h->lat[h->t & 1], h->d.storage, h->P, h->d.nx, h->d.ny, h->n_probes, h->probe_xyz,
+        CK(stg::launch_probe(h->lat[h->t & 1], h->d.storage, lattice_view(h), h->n_probes, h->probe_xyz,
                              (float)h->d.force[0], (float)h->d.force[1], (float)h->d.force[2],
                              h->probe_buf + (size_t)s * h->n_probes * 3, h->stream));
     }
@@ -1155,15 +1258,36 @@ int stg_lbm_get_tile(const stg_lbm *h, stg_tile *tile)
 namespace stg {
 namespace host {
 
-cudaError_t trial_pass(stg_lbm *h, const stg_tile &tile, cudaStream_t s)
+cudaError_t trial_pass(stg_lbm *h, const stg_tile &tile, cudaStream_t s, int k)
 {
-    const int parity = (int)(h->t & 1);
+    const int parity = (int)((h->t + (h->aa ? k : 0)) & 1);
     const stg_tile keep = h->tile;
     h->tile = tile;
     stg::StepArgs a = step_args(h, parity);
     h->tile = keep;
     a.stats_every = 0;  // the edge kernel samples on its own otherwise
     return stg::launch_step(a, h->d.storage, h->d.collision, false, s, h->side, h->ev_fork, h->ev_join);
+}
+
+int save_trial_state(stg_lbm *h, std::vector<unsigned char> &pops, stg::StepCtl &ctl)
+{
+    if (!h->aa) return STG_OK;
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    pops.resize(19 * h->P * h->elem);
+    CK(cudaMemcpy(pops.data(), h->lat[0], pops.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&ctl, h->ctl, sizeof ctl, cudaMemcpyDeviceToHost));
+    return STG_OK;
+}
+
+int restore_trial_state(stg_lbm *h, const std::vector<unsigned char> &pops, const stg::StepCtl &ctl)
+{
+    if (!h->aa) return STG_OK;
+    int rc = wait_stream(h);
+    if (rc) return rc;
+    CK(cudaMemcpy(h->lat[0], pops.data(), pops.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice));
+    return STG_OK;
 }
 
 int apply_tile(stg_lbm *h, const stg_tile &tile)
@@ -1213,14 +1337,18 @@ int stg_lbm_autotune(stg_lbm *h, int32_t trial_passes, stg_tile *chosen)
     }
     // plain passes from the current state: src = lat[t & 1], dst = lat[(t & 1) ^ 1];
     // the pass writes the device counter t[p ^ 1] = t + 1, which the next real
-    // step writes again, and the mass slots, which every pass rewrites
+    // step writes again, and the mass slots, which every pass rewrites.  In
+    // place the passes update the lattice, which is saved first and put back.
+    std::vector<unsigned char> keep;
+    StepCtl keep_ctl{};
+    rc = save_trial_state(h, keep, keep_ctl);
     stg_tile best = h->tile;
     float best_ms = -1.f;
     for (int c = 0; c < ncand && rc == STG_OK; ++c) {
         cudaError_t e = cudaSuccess;
         for (int k = 0; k <= trial_passes && e == cudaSuccess; ++k) {
             if (k == 1) e = cudaEventRecord(e0, h->stream);
-            if (e == cudaSuccess) e = trial_pass(h, cand[c], h->stream);
+            if (e == cudaSuccess) e = trial_pass(h, cand[c], h->stream, k);
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1234,7 +1362,9 @@ int stg_lbm_autotune(stg_lbm *h, int32_t trial_passes, stg_tile *chosen)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    const int rc2 = restore_trial_state(h, keep, keep_ctl);
     if (rc) return rc;
+    if (rc2) return rc2;
     rc = apply_tile(h, best);
     if (rc == STG_OK && chosen) *chosen = best;
     return rc;

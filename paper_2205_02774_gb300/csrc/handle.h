@@ -19,6 +19,7 @@ struct stg_lbm {
     stg_domain d{};
     stg_params p{};
     bool inout = false;
+    bool aa = false;  // one lattice updated in place (lat[1] == lat[0])
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -92,8 +93,15 @@ int queue_check_readback(stg_lbm *h, int64_t t_before);
 int wait_stream(stg_lbm *h);
 // one plain (non-sampling) step pass from the current state with `tile`, on
 // stream s; it does not advance the step counter, the filter or the
-// statistics (it recomputes what the next real step writes)
-cudaError_t trial_pass(stg_lbm *h, const stg_tile &tile, cudaStream_t s);
+// statistics (two lattices: it recomputes what the next real step writes).
+// In place the pass updates the lattice: the k-th pass of a trial series
+// takes the parity of step t + k (so the arrangement stays valid), and the
+// caller brackets the series with save_trial_state / restore_trial_state.
+cudaError_t trial_pass(stg_lbm *h, const stg_tile &tile, cudaStream_t s, int k = 0);
+// in place only: copy the populations and the device step counters to host
+// memory before a trial series, and back afterwards (no-ops for two lattices)
+int save_trial_state(stg_lbm *h, std::vector<unsigned char> &pops, stg::StepCtl &ctl);
+int restore_trial_state(stg_lbm *h, const std::vector<unsigned char> &pops, const stg::StepCtl &ctl);
 // set the tile and re-capture the handle's own graphs
 int apply_tile(stg_lbm *h, const stg_tile &tile);
 // the autotuner's candidate tiles

@@ -11,7 +11,19 @@
 // the y part and the z part (tables built in FP64 on the host) and the time
 // part phi^n + omega^n t (evaluated in FP64 per block); their FP32 sum is
 // below 6 pi whatever the step count and is reduced to [-pi, pi] before the
-// cosine.  Each block serves 32 nodes; its 8 warps split the mode sum.
+// cosine.
+//
+// Work split: a block covers 32 consecutive j (one per lane) by 8 span nodes
+// k; its 8 warps are 4 pairs of span nodes times 2 halves of the mode sum
+// (modes of even and odd index within a chunk).  Everything a mode term
+// needs is staged in shared memory per chunk of INLET_CHUNK modes by
+// coalesced loads of the whole block (any mode count fits the fixed
+// footprint): the time phase and sigma^n, the block's 8 z parts, and its 32
+// y parts and amplitudes sqrt(6 q^n(j)).  A thread reads the y part and the
+// amplitude of a mode once and uses them for its two span nodes, so a mode
+// term costs a few shared-memory reads, the phase sum and its reduction, one
+// cosine and four multiply-adds; the two halves of the mode sum are added in
+// a fixed order at the end.
 // The plane of step t + 1 is computed during step t (ahead = 1), beside the
 // step pass that reads the plane of step t; the first plane after a reset is
 // computed with ahead = 0.
@@ -19,82 +31,117 @@
 
 namespace stg {
 
-constexpr int INLET_NODES = 32;  // nodes per block (one per lane)
-constexpr int INLET_WARPS = 8;   // the mode sum of each node is split over 8 warps
+constexpr int INLET_J = 32;      // wall-normal nodes per block (one per lane)
+constexpr int INLET_KPT = 2;     // span nodes per thread
+constexpr int INLET_KG = 4;      // span-node pairs per block
+constexpr int INLET_H = 2;       // halves of the mode sum
+constexpr int INLET_WARPS = INLET_KG * INLET_H;
+constexpr int INLET_K = INLET_KPT * INLET_KG;  // span nodes per block
+constexpr int INLET_CHUNK = 128; // modes staged per pass through shared memory
 constexpr double TWO_PI = 6.283185307179586476925286766559;
 
-__global__ void __launch_bounds__(INLET_NODES *INLET_WARPS) stg_inlet_kernel(const InletArgs a)
+__global__ void __launch_bounds__(INLET_J *INLET_WARPS) stg_inlet_kernel(const InletArgs a)
 {
-    extern __shared__ float sm[];  // theta[N], sigma[3N]
-    __shared__ float part[INLET_WARPS][3][INLET_NODES];
-    float *theta = sm;
-    float *sig = sm + a.N;
-    const int tid = threadIdx.y * INLET_NODES + threadIdx.x;
+    __shared__ float4 ts[INLET_CHUNK];           // (time phase, sigma_x, sigma_y, sigma_z) per mode
+    __shared__ float2 bz[INLET_CHUNK][INLET_KG]; // z parts of the block's span nodes per mode
+    __shared__ float ay_s[INLET_CHUNK][INLET_J]; // y parts of the block's wall-normal nodes per mode
+    __shared__ float sq_s[INLET_CHUNK][INLET_J]; // amplitudes sqrt(6 q^n(j)) per mode
+    __shared__ float part[INLET_KG][INLET_KPT][3][INLET_J];  // second half of the mode sum
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int g = w % INLET_KG, h = w / INLET_KG;
+    const int tid = w * INLET_J + lane;
+    const int ny = a.ny, nz = a.nz, N = a.N;
+    const int j0 = blockIdx.x * INLET_J;
+    const int j = j0 + lane;
+    const int k0 = blockIdx.y * INLET_K;
+    const bool jl = j < ny;
     const long long t = a.ctl->t[a.parity] + a.ahead;
     const bool first = (t == a.ctl->t0_filter);
-    // time part of the phase, phi^n + omega^n t, reduced to [0, 2 pi) in FP64
-    for (int n = tid; n < a.N; n += INLET_NODES * INLET_WARPS) {
-        double th = a.phi[n] + a.omg[n] * (double)t;
-        th -= TWO_PI * floor(th / TWO_PI);
-        theta[n] = (float)th;
-        sig[3 * n + 0] = a.sig[3 * n + 0];
-        sig[3 * n + 1] = a.sig[3 * n + 1];
-        sig[3 * n + 2] = a.sig[3 * n + 2];
-    }
-    __syncthreads();
-    const int ny = a.ny, nz = a.nz;
-    const int node = blockIdx.x * INLET_NODES + threadIdx.x;
-    const bool live = node < ny * nz;
-    const int j = live ? node % ny : 0, k = live ? node / ny : 0;
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-    if (live) {
-        for (int n = threadIdx.y; n < a.N; n += INLET_WARPS) {
-            float arg = a.A[(size_t)n * ny + j] + a.B[(size_t)n * nz + k] + theta[n];  // in [0, 6 pi)
-            arg -= 6.2831853f * rintf(arg * 0.15915494f);                             // to [-pi, pi]
-            const float amp = a.SQ[(size_t)n * ny + j] * __cosf(arg);
-            v0 = fmaf(amp, sig[3 * n + 0], v0);
-            v1 = fmaf(amp, sig[3 * n + 1], v1);
-            v2 = fmaf(amp, sig[3 * n + 2], v2);
+    float v[INLET_KPT][3];
+#pragma unroll
+    for (int q = 0; q < INLET_KPT; ++q) v[q][0] = v[q][1] = v[q][2] = 0.f;
+    for (int n0 = 0; n0 < N; n0 += INLET_CHUNK) {
+        const int cn = min(INLET_CHUNK, N - n0);
+        __syncthreads();  // the previous chunk is consumed
+        for (int m = tid; m < cn; m += INLET_J * INLET_WARPS) {
+            const int n = n0 + m;
+            // time part of the phase, phi^n + omega^n t, reduced to [0, 2 pi) in FP64
+            double th = a.phi[n] + a.omg[n] * (double)t;
+            th -= TWO_PI * floor(th * (1.0 / TWO_PI));  // within a few ulp of [0, 2 pi)
+            ts[m] = make_float4((float)th, a.sig[3 * n + 0], a.sig[3 * n + 1], a.sig[3 * n + 2]);
+        }
+        for (int e = tid; e < cn * INLET_K; e += INLET_J * INLET_WARPS) {
+            const int m = e / INLET_K, kk = e % INLET_K;
+            const int k = min(k0 + kk, nz - 1);  // span nodes past nz are computed and not stored
+            reinterpret_cast<float *>(&bz[m][0])[kk] = a.B[(size_t)(n0 + m) * nz + k];
+        }
+        for (int e = tid; e < cn * INLET_J; e += INLET_J * INLET_WARPS) {
+            const int m = e / INLET_J, jj = min(j0 + e % INLET_J, ny - 1);  // rows past ny are not stored
+            ay_s[m][e % INLET_J] = a.A[(size_t)(n0 + m) * ny + jj];
+            sq_s[m][e % INLET_J] = a.SQ[(size_t)(n0 + m) * ny + jj];
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int m = h; m < cn; m += INLET_H) {
+            const float4 tm = ts[m];
+            const float ay = ay_s[m][lane] + tm.x;  // in [0, 4 pi)
+            const float sq = sq_s[m][lane];
+            const float2 b2 = bz[m][g];
+            const float bq[INLET_KPT] = {b2.x, b2.y};
+#pragma unroll
+            for (int q = 0; q < INLET_KPT; ++q) {
+                float arg = ay + bq[q];                           // in [0, 6 pi)
+                arg -= 6.2831853f * rintf(arg * 0.15915494f);     // to [-pi, pi]
+                const float amp = sq * __cosf(arg);
+                v[q][0] = fmaf(amp, tm.y, v[q][0]);
+                v[q][1] = fmaf(amp, tm.z, v[q][1]);
+                v[q][2] = fmaf(amp, tm.w, v[q][2]);
+            }
         }
     }
-    part[threadIdx.y][0][threadIdx.x] = v0;
-    part[threadIdx.y][1][threadIdx.x] = v1;
-    part[threadIdx.y][2][threadIdx.x] = v2;
-    __syncthreads();
-    if (threadIdx.y != 0 || !live) return;
-    v0 = v1 = v2 = 0.f;
+    if (h == 1) {
 #pragma unroll
-    for (int w = 0; w < INLET_WARPS; ++w) {
-        v0 += part[w][0][threadIdx.x];
-        v1 += part[w][1][threadIdx.x];
-        v2 += part[w][2][threadIdx.x];
+        for (int q = 0; q < INLET_KPT; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) part[g][q][c][lane] = v[q][c];
     }
+    __syncthreads();
+    if (h == 1 || !jl) return;
     const float *L = a.a6 + 6 * j;
-    const float u0 = L[0] * v0;
-    const float u1 = L[1] * v0 + L[2] * v1;
-    const float u2 = L[3] * v0 + L[4] * v1 + L[5] * v2;
+    const float l11 = L[0], l21 = L[1], l22 = L[2], l31 = L[3], l32 = L[4], l33 = L[5];
+    const float af = a.a_filter, bf = 1.0f - a.a_filter, ui = a.u_int[j];
     const size_t plane = (size_t)ny * nz;
-    float f0 = u0, f1 = u1, f2 = u2;
-    if (!first) {
-        const float af = a.a_filter, bf = 1.0f - a.a_filter;
-        f0 = af * a.uf[node] + bf * u0;
-        f1 = af * a.uf[plane + node] + bf * u1;
-        f2 = af * a.uf[2 * plane + node] + bf * u2;
+#pragma unroll
+    for (int q = 0; q < INLET_KPT; ++q) {
+        const int k = k0 + g * INLET_KPT + q;
+        if (k >= nz) break;
+        const float v0 = v[q][0] + part[g][q][0][lane];
+        const float v1 = v[q][1] + part[g][q][1][lane];
+        const float v2 = v[q][2] + part[g][q][2][lane];
+        const size_t node = (size_t)k * ny + j;
+        const float u0 = l11 * v0;
+        const float u1 = l21 * v0 + l22 * v1;
+        const float u2 = l31 * v0 + l32 * v1 + l33 * v2;
+        float f0 = u0, f1 = u1, f2 = u2;
+        if (!first) {
+            f0 = af * a.uf[node] + bf * u0;
+            f1 = af * a.uf[plane + node] + bf * u1;
+            f2 = af * a.uf[2 * plane + node] + bf * u2;
+        }
+        a.uf[node] = f0;
+        a.uf[plane + node] = f1;
+        a.uf[2 * plane + node] = f2;
+        a.ubc[node] = ui + f0;
+        a.ubc[plane + node] = f1;
+        a.ubc[2 * plane + node] = f2;
     }
-    a.uf[node] = f0;
-    a.uf[plane + node] = f1;
-    a.uf[2 * plane + node] = f2;
-    a.ubc[node] = a.u_int[j] + f0;
-    a.ubc[plane + node] = f1;
-    a.ubc[2 * plane + node] = f2;
 }
 
 cudaError_t launch_inlet(const InletArgs &a, cudaStream_t s)
 {
-    const int nodes = a.ny * a.nz;
-    const int blocks = (nodes + INLET_NODES - 1) / INLET_NODES;
-    const size_t smem = sizeof(float) * 4 * (size_t)(a.N > 0 ? a.N : 1);
-    stg_inlet_kernel<<<blocks, dim3(INLET_NODES, INLET_WARPS), smem, s>>>(a);
+    const dim3 grid((a.ny + INLET_J - 1) / INLET_J, (a.nz + INLET_K - 1) / INLET_K);
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;  // nz > 524 280
+    stg_inlet_kernel<<<grid, dim3(INLET_J, INLET_WARPS), 0, s>>>(a);
     return cudaGetLastError();
 }
 

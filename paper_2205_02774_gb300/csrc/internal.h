@@ -31,6 +31,7 @@ struct StepArgs {
     void *dstp[19];
     int il, ir;             // 32-wide x chunks [il, ir) of rows 1..ny-2 belong to the interior kernel
     int interior;           // interior kernel: 0 best available, 1 one cell per thread, 2 cell pairs
+    int aa;                 // 1: one lattice updated in place (AA pattern; src == dst), 0: two lattices
     // tile of the plain (non-sampling) vector launches: layout 0 = 8 z-warps on one 64-cell x chunk,
     // layout 1 = 4 x-warps (256 cells) walking z together; zc / wall_zc = z planes per block of the
     // rows 1..ny-2 / wall-row launch (0: the whole z column)
@@ -96,12 +97,23 @@ cudaError_t launch_inlet(const InletArgs &a, cudaStream_t s);
 cudaError_t launch_setup_nodes(int ny, int N, const double *R6, const double *le, const double *leta,
                                const double *lcut, const double *kn, const double *dk, float *a6,
                                float *SQ, cudaStream_t s);
-cudaError_t launch_init_equilibrium(void *dst, int storage, int nx, int ny, int nz, const float *u_int,
+// swap: store population i in slot opp(i) (the in-place layout before a step of even index)
+cudaError_t launch_init_equilibrium(void *dst, int storage, int nx, int ny, int nz, const float *u_int, int swap,
                                     cudaStream_t s);
 cudaError_t launch_mass(const MassArgs &a, cudaStream_t s);
+// How to find a population in a stored lattice: slot i of the cell for two
+// lattices, the in-place arrangement after t completed steps otherwise.
+struct LatticeView {
+    int nx, ny, nz, bc_x, bc_y, aa;
+    size_t P;
+    long long t;
+};
 // velocity of n cells (xyz: device int triples) of a stored lattice into out[3 n]
-cudaError_t launch_probe(const void *src, int storage, size_t P, int nx, int ny, int n, const int *xyz, float Fx,
+cudaError_t launch_probe(const void *src, int storage, const LatticeView &lv, int n, const int *xyz, float Fx,
                          float Fy, float Fz, float *out, cudaStream_t s);
+// canonical sub-block [19][bz][by][bx] of a stored lattice into device memory `out`
+cudaError_t launch_gather_block(const void *src, int storage, const LatticeView &lv, int x0, int y0, int z0, int bx,
+                                int by, int bz, void *out, cudaStream_t s);
 
 // Upper bound of the mass-partial slots of one step pass over every tile
 // that set_tile accepts (z chunks of at least MIN_ZC planes).

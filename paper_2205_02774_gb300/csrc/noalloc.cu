@@ -38,7 +38,7 @@ extern "C" int stg_lattice_mass_noalloc(const void *pops, int32_t storage, int32
         stg::record_error("stg_lattice_mass_noalloc: NULL pointer");
         return STG_ERR_INVALID;
     }
-    if (storage != STG_FP32 && storage != STG_FP16_SHIFTED) {
+    if (storage != STG_FP32 && storage != STG_FP16_SHIFTED && storage != STG_FP16_SHIFTED_SR) {
         stg::record_error("stg_lattice_mass_noalloc: bad storage");
         return STG_ERR_INVALID;
     }

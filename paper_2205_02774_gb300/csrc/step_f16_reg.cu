@@ -1,0 +1,12 @@
+// Step kernels of shifted binary16 storage with the regularized collision (one of four
+// instantiation units of step_kernel.cuh, compiled in parallel).
+#include "step_kernel.cuh"
+
+namespace stg {
+
+bool launch_f16_reg(const StepArgs &a, bool stats, cudaStream_t s, cudaStream_t side)
+{
+    return launch_typed<__half, true>(a, stats, s, side);
+}
+
+}  // namespace stg

@@ -23,7 +23,7 @@ def pair(case, **kw):
     from paper_2205_02774_gb300.channel import Channel
     gpu = Channel.from_case(case, **{k: v for k, v in kw.items() if k not in ("oracle_nx",)})
     okw = {k: v for k, v in kw.items() if k not in ("storage", "check_every", "mass_tol", "oracle_nx",
-                                                      "use_torch_allocator", "stream")}
+                                                      "use_torch_allocator", "stream", "streaming")}
     if "oracle_nx" in kw:
         c2 = case.with_(nx=kw["oracle_nx"])
         orc = O.Sim.from_case(c2, **okw)

@@ -1,8 +1,10 @@
-"""The refined channel (h = 128, 1536 x 256 x 384, 151M cells) in FP32 and in
-shifted-FP16 storage: one step from the GPU's own state checked cell by cell
-against the oracle on a 64^3 sub-block (the oracle reads the sub-block and a
-one-cell halo), and the FP16 run's mean and Reynolds-stress sums against the
-FP32 run's after 200 steps (within 1 %, normwise)."""
+"""The precision form: the refined channel (h = 128, 1536 x 256 x 384, 151M
+cells) in FP32 and in shifted-FP16 storage, one step from the GPU's own state
+checked cell by cell against the oracle on a 64^3 sub-block (the oracle reads
+the sub-block and a one-cell halo); and the turbulent statistics of an FP16
+run (stochastic rounding) against the FP32 run over more than one
+flow-through of the production channel (mean velocity and fluctuating
+Reynolds stresses within 1 %)."""
 import numpy as np
 import pytest
 
@@ -57,16 +59,56 @@ def test_refined_subblock_one_step(storage):
         assert worst <= 0
 
 
-def test_refined_fp16_profiles_vs_fp32():
+def _profiles(st, nz):
+    """Mean velocity and fluctuating stresses <u'_a u'_b> = <u_a u_b> - <u_a><u_b>
+    per (x, y), averaged over z and the sampled steps."""
+    n = st["n_samples"] * nz
+    mean = st["mean_sum"] / n
+    rey = st["rey_sum"] / n
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    cov = np.stack([rey[k] - mean[a] * mean[b] for k, (a, b) in enumerate(pairs)])
+    return mean, cov
+
+
+def test_turbulent_fp16_vs_fp32_profiles():
+    """The 768 x 128 x 192 channel (h = 64) in binary16 storage written by
+    stochastic rounding and in FP32 storage for more than one flow-through
+    (nx / U_b steps), statistics restarted half way so that they cover the
+    second half: the mean velocity and each fluctuating Reynolds stress
+    <u'_a u'_b>, per (x, y), agree within 1 % normwise (max abs difference /
+    max abs FP32 value); the stresses the RANS input sets to zero (xz, yz)
+    within 1 % of the largest normal stress.  (Round-to-nearest binary16
+    misses this bound: in the slowly developing flow it drops updates below
+    half a spacing every step, and its profiles drift by a few per cent
+    towards the outlet.)"""
     from paper_2205_02774_gb300.channel import Channel
+    c = case("channel_768x128x192")
+    total, restart = 32000, 16000
     out = {}
-    for storage in ("fp32", "fp16s"):
-        g = Channel.from_case(REFINED.with_(storage=storage), check_every=50, mass_tol=0.1)
-        g.step(200)
+    for storage in ("fp32", "fp16sr"):
+        g = Channel.from_case(c.with_(storage=storage), check_every=1000, mass_tol=0.5)
+        U_b = g.info()["U_b"]
+        g.step(restart)
+        g.reset_stats()
+        g.step(total - restart)
         st = g.stats()
         g.close()
         assert st["rc"] == 0, st["error"]
-        assert st["n_samples"] == 20
-        out[storage] = st
-    assert normwise(out["fp16s"]["mean_sum"], out["fp32"]["mean_sum"]) < 1e-2
-    assert normwise(out["fp16s"]["rey_sum"], out["fp32"]["rey_sum"]) < 1e-2
+        assert st["n_samples"] == (total - restart) // c.stats_every
+        out[storage] = _profiles(st, c.nz)
+    assert total >= c.nx / U_b  # at least one flow-through
+    m32, r32 = out["fp32"]
+    m16, r16 = out["fp16sr"]
+    errs = {"U": normwise(m16[0], m32[0])}
+    names = ["uu", "vv", "ww", "uv", "uw", "vw"]
+    for k in range(4):
+        errs[names[k]] = normwise(r16[k], r32[k])
+    big = np.abs(r32[:3]).max()
+    for k in (4, 5):
+        errs[names[k]] = float(np.abs(r16[k] - r32[k]).max() / big)
+    scale = {"U_max": float(np.abs(m32[0]).max()), "uu_max": float(np.abs(r32[0]).max()),
+             "uv_max": float(np.abs(r32[3]).max()), "uw_max": float(np.abs(r32[4]).max())}
+    print("fp16 (stochastic rounding) vs fp32 profile errors", errs, scale)
+    assert scale["uu_max"] > 1e-3 * scale["U_max"] ** 2  # the fluctuations are resolved, not noise
+    for k, v in errs.items():
+        assert v < 1e-2, (k, v, errs)

@@ -32,7 +32,8 @@ class ChannelCase:
     stats_every: int = 10
     t_filter: float = 4.0
     mach_target: float = 0.0516
-    storage: str = "fp32"      # "fp32" | "fp16s" (f - w_i stored as binary16)
+    storage: str = "fp32"      # "fp32" | "fp16s" (f - w_i stored as binary16) | "fp16sr" (same, stochastic rounding)
+    streaming: str = "pull"    # "pull" (two lattices) | "aa" (one lattice updated in place)
     collision: str = "regularized"  # "regularized" | "bgk"
     bc_x: str = "stg"          # "stg" (inlet/outlet) | "periodic"
     bc_y: str = "walls"        # "walls" | "periodic"
