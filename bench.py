@@ -511,7 +511,7 @@ def ensemble_run(members, steps, warmup, storage):
     return out
 
 
-def serve_run(n_jobs, steps_scale):
+def serve_run(n_jobs, steps_scale, streaming="pull"):
     """Served stream: Poisson arrivals (2 jobs/s) of channel jobs of 0.5M-20M
     cells (h = 20..65, aspect 12:2:3), Re_tau from {180, 395}, FP32 or FP16
     storage, own seeds, step counts uniform in [1000, 20000] x steps_scale,
@@ -521,7 +521,8 @@ def serve_run(n_jobs, steps_scale):
     from paper_2205_02774_gb300.serving import serve
     from workloads.serving import poisson_stream
     sm = max(1, int(round(1000 * steps_scale)))
-    jobs = poisson_stream(n_jobs, rate_per_s=2.0, steps_min=sm, steps_max=max(sm, int(round(20000 * steps_scale))))
+    jobs = poisson_stream(n_jobs, rate_per_s=2.0, steps_min=sm, steps_max=max(sm, int(round(20000 * steps_scale))),
+                          streaming=streaming)
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     results, rep = serve(jobs, hbm_budget_bytes=150e9, check_every=100, mass_tol=0.5)
@@ -529,6 +530,7 @@ def serve_run(n_jobs, steps_scale):
     offered = sum(j.case.cells * j.steps for j in jobs) / max(jobs[-1].arrival_s, 1e-9) / 1e6
     return {"workload": f"served stream of {len(jobs)} jobs", "value": rep["jobs_per_s"], "unit": "jobs/s",
             "arrival_rate_per_s": 2.0, "steps_scale": steps_scale, "steps_range": [sm, int(round(20000 * steps_scale))],
+            "streaming": streaming,
             "hbm_budget_gb": 150,
             "aggregate_mlups": rep["aggregate_mlups"], "offered_mlups": offered,
             "p50_latency_s": rep["p50_latency_s"], "p99_latency_s": rep["p99_latency_s"],
@@ -557,7 +559,7 @@ def run_serve(args):
     """--workload serve: the served stream alone as the bench line."""
     from paper_2205_02774_gb300 import build
     build()
-    s = serve_run(args.jobs, args.serve_steps_scale)
+    s = serve_run(args.jobs, args.serve_steps_scale, args.streaming)
     line = {"metric": "jobs/s", "value": s["value"], "unit": "jobs/s", "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic", "dtype": "f32",
             "config": {"workload": s["workload"], "arrival_rate_per_s": 2.0,

@@ -32,8 +32,21 @@ __global__ void stats_reduce_kernel(const float *part, int groups, size_t m, dou
 {
     const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;  // q * m + xy
     if (k >= 9 * m) return;
-    double sum = 0.0;
-    for (int g = 0; g < groups; ++g) sum += (double)part[(size_t)g * 9 * m + k];
+    // the groups in index order as a compensated FP32 sum (the two-sum error
+    // of every addition is kept: hi + lo holds the sum to about 2^-44 of its
+    // size), then one FP64 addition into the running sum; GB300's FP64 rate
+    // is a small fraction of its FP32 rate, and an FP64 conversion and add per
+    // group made this kernel FP64-bound
+    float hi = 0.f, lo = 0.f;
+#pragma unroll 4
+    for (int g = 0; g < groups; ++g) {
+        const float x = __ldcs(part + (size_t)g * 9 * m + k);
+        const float s = hi + x;
+        const float z = s - hi;
+        lo += (hi - (s - z)) + (x - z);
+        hi = s;
+    }
+    const double sum = (double)hi + (double)lo;
     if (k < 3 * m) stat_mean[k] += sum;
     else stat_rey[k - 3 * m] += sum;
 }

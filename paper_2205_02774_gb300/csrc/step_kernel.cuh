@@ -709,23 +709,24 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
 
 // Sampling-step vector kernel over all x of rows 1..ny-2 (YEDGE false) or of
 // rows 0 and ny-1 (YEDGE true; that launch also advances the device step
-// counter).  Block (x chunk, row, group of STAT_GROUP z planes); its 8 warps
-// take every 8th plane of the group, so the block sums the group's velocity moments per
-// (x, y) in shared memory and writes them, in FP32, to the group's slot of
-// a.stat_part; stats_reduce_kernel then adds the groups in order in FP64.
-// The decomposition is fixed (no tile), so the statistics are deterministic
-// and independent of the launch tile.  H16 as in vec_loop; the binary16
-// regularized unforced interior instance fits 64 registers (32 warps per SM).  STATS is chosen on the host (it knows
-// the step count); plain steps use lbm_vec_zc_kernel.
+// counter).  Block (4 consecutive 64-cell x chunks, row, group of STAT_GROUP
+// z planes); each warp walks the group's planes in order for its own chunk
+// (the plain kernel's layout 1), its lanes adding the velocity moments of
+// their cells to private shared-memory slots, and writes the group's FP32
+// sums per (x, y) to the group's slot of a.stat_part; stats_reduce_kernel
+// then adds the groups in order.  The decomposition is fixed (no tile), so
+// the statistics are deterministic and independent of the launch tile.
+// H16 as in vec_loop.  STATS is chosen on the host (it knows the step
+// count); plain steps use lbm_vec_zc_kernel.
+constexpr int STAT_NW = 4;  // warps (x chunks) per sampling block
 template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP, bool H16, int MODE, bool SR>
-__global__ void __launch_bounds__(BX *BZ, (REG && (!STATS || (H16 && !FORCE && !YEDGE))) ? 4 : 3)
-    lbm_vec_kernel(const StepArgs a)
+__global__ void __launch_bounds__(BX *STAT_NW, (REG && !FORCE && !YEDGE) ? 8 : 6) lbm_vec_kernel(const StepArgs a)
 {
     constexpr int CPL = VecOf<S>::CPL;
-    __shared__ float sacc[STATS ? BZ : 1][9][BX * CPL];  // per-thread statistics slots
+    __shared__ float sacc[STATS ? STAT_NW : 1][9][BX * CPL];  // per-thread statistics slots
     const int nx = a.nx, ny = a.ny;
     const int lane = threadIdx.x, wi = threadIdx.y;
-    const int x0 = BX * CPL * blockIdx.x;
+    const int x0 = BX * CPL * (STAT_NW * blockIdx.x + wi);
     const int y = YEDGE ? (blockIdx.y == 0 ? 0 : ny - 1) : blockIdx.y + 1;
     const long long t = a.ctl->t[a.parity];
     const bool do_check = a.check_every > 0 && ((t + 1) % a.check_every) == 0;
@@ -735,30 +736,23 @@ __global__ void __launch_bounds__(BX *BZ, (REG && (!STATS || (H16 && !FORCE && !
 #pragma unroll
             for (int j = 0; j < CPL; ++j) sacc[wi][q][CPL * lane + j] = 0.f;
     }
-    static_assert(STAT_GROUP % BZ == 0, "whole planes per warp");
     const int zb = STATS ? blockIdx.z * STAT_GROUP : 0;
-    const float sdr = vec_loop<S, REG, FORCE, STATS, YEDGE, SP, H16, MODE, SR>(a, sacc, x0, y, zb + wi, STATS ? min(zb + STAT_GROUP, a.nz) : a.nz, BZ);
+    const float sdr = vec_loop<S, REG, FORCE, STATS, YEDGE, SP, H16, MODE, SR>(
+        a, sacc, x0, y, zb, STATS ? min(zb + STAT_GROUP, a.nz) : a.nz, 1);
     if (STATS) {
-        __syncthreads();
-        if (wi == 0) {
-            const size_t m = (size_t)nx * ny;
-            float *part = a.stat_part + (size_t)blockIdx.z * 9 * m;
+        // each thread wrote only its own slots: no barrier
+        const size_t m = (size_t)nx * ny;
+        float *part = a.stat_part + (size_t)blockIdx.z * 9 * m;
 #pragma unroll
-            for (int j = 0; j < CPL; ++j) {
-                const int xc = x0 + CPL * lane + j;
-                if (xc >= nx) continue;
-                const size_t xy = (size_t)y * nx + xc;
+        for (int j = 0; j < CPL; ++j) {
+            const int xc = x0 + CPL * lane + j;
+            if (xc >= nx) continue;
+            const size_t xy = (size_t)y * nx + xc;
 #pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    float sum = 0.f;
-#pragma unroll
-                    for (int k = 0; k < BZ; ++k) sum += sacc[k][q][CPL * lane + j];
-                    part[q * m + xy] = sum;
-                }
-            }
+            for (int q = 0; q < 9; ++q) part[q * m + xy] = sacc[wi][q][CPL * lane + j];
         }
     }
-    if (do_check) mass_finish<BX * BZ>(a, sdr);
+    if (do_check) mass_finish<BX * STAT_NW>(a, sdr);
     if (YEDGE && a.bump_t && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && lane == 0 && wi == 0)
         a.ctl->t[a.parity ^ 1] = t + 1;
 }
@@ -878,7 +872,9 @@ static void launch_vec(StepArgs a, const Split &sp, bool stats, cudaStream_t s, 
         // sums go to a.stat_part and are reduced after the pass); plain steps
         // take the tile's z chunks
         const int groups = (nz + STAT_GROUP - 1) / STAT_GROUP;
-        dim3 gi(sp.nxv, rows_in, groups), ge(sp.nxv, rows_edge, groups);
+        const int nxs = (nx + BX * cpl * STAT_NW - 1) / (BX * cpl * STAT_NW);  // sampling blocks along x
+        dim3 gi(nxs, rows_in, groups), ge(nxs, rows_edge, groups);
+        const dim3 bs(BX, STAT_NW);
         dim3 bi = block;
         if (!stats) {
             const int zc = a.tile_zc > 0 ? a.tile_zc : nz, wzc = a.tile_wall_zc > 0 ? a.tile_wall_zc : nz;
@@ -903,15 +899,15 @@ static void launch_vec(StepArgs a, const Split &sp, bool stats, cudaStream_t s, 
         ae.slot_base = n_in;
         ae.bump_t = 1;
         if (n_in > 0) {
-            if (stats && h16) lbm_vec_kernel<S, REG, FORCE, true, false, SP, H, MODE, SR><<<gi, block, 0, s>>>(ai);
-            else if (stats) lbm_vec_kernel<S, REG, FORCE, true, false, SP, false, MODE, SR><<<gi, block, 0, s>>>(ai);
+            if (stats && h16) lbm_vec_kernel<S, REG, FORCE, true, false, SP, H, MODE, SR><<<gi, bs, 0, s>>>(ai);
+            else if (stats) lbm_vec_kernel<S, REG, FORCE, true, false, SP, false, MODE, SR><<<gi, bs, 0, s>>>(ai);
             else if (h16 && a.tile_layout == 1) lbm_vec_zc_kernel<S, REG, FORCE, 1, false, SP, H, MODE, SR><<<gi, bi, 0, s>>>(ai);
             else if (h16) lbm_vec_zc_kernel<S, REG, FORCE, 0, false, SP, H, MODE, SR><<<gi, bi, 0, s>>>(ai);
             else if (a.tile_layout == 1) lbm_vec_zc_kernel<S, REG, FORCE, 1, false, SP, false, MODE, SR><<<gi, bi, 0, s>>>(ai);
             else lbm_vec_zc_kernel<S, REG, FORCE, 0, false, SP, false, MODE, SR><<<gi, bi, 0, s>>>(ai);
         }
-        if (stats && h16) lbm_vec_kernel<S, REG, FORCE, true, true, SP, H, MODE, SR><<<ge, block, 0, side>>>(ae);
-        else if (stats) lbm_vec_kernel<S, REG, FORCE, true, true, SP, false, MODE, SR><<<ge, block, 0, side>>>(ae);
+        if (stats && h16) lbm_vec_kernel<S, REG, FORCE, true, true, SP, H, MODE, SR><<<ge, bs, 0, side>>>(ae);
+        else if (stats) lbm_vec_kernel<S, REG, FORCE, true, true, SP, false, MODE, SR><<<ge, bs, 0, side>>>(ae);
         else if (h16) lbm_vec_zc_kernel<S, REG, FORCE, 0, true, SP, H, MODE, SR><<<ge, block, 0, side>>>(ae);
         else lbm_vec_zc_kernel<S, REG, FORCE, 0, true, SP, false, MODE, SR><<<ge, block, 0, side>>>(ae);
     }

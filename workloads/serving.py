@@ -30,9 +30,9 @@ class Job:
     steps: int
 
 
-def channel_case(h, re_tau=180.0, storage="fp32", seed=0, n_modes=200, n_fv=96, stats_every=10):
+def channel_case(h, re_tau=180.0, storage="fp32", seed=0, n_modes=200, n_fv=96, stats_every=10, streaming="pull"):
     return ChannelCase(f"channel_h{h}", 12 * h, 2 * h, 3 * h, n_modes=n_modes, n_fv=n_fv, re_tau=float(re_tau),
-                       seed=int(seed), storage=storage, stats_every=stats_every)
+                       seed=int(seed), storage=storage, stats_every=stats_every, streaming=streaming)
 
 
 def ensemble(n, heights=(16, 24, 32, 48, 64), re_taus=(180, 395), steps=5000, draw_seed=12345, storage="fp32",
@@ -47,7 +47,7 @@ def ensemble(n, heights=(16, 24, 32, 48, 64), re_taus=(180, 395), steps=5000, dr
 
 
 def poisson_stream(n, rate_per_s=2.0, min_cells=0.5e6, max_cells=20e6, steps_min=1000, steps_max=20000,
-                   storages=("fp32", "fp16s"), re_taus=(180, 395), seed=7, n_modes=200):
+                   storages=("fp32", "fp16s"), re_taus=(180, 395), seed=7, n_modes=200, streaming="pull"):
     rng = np.random.default_rng(seed)
     hs = [h for h in range(2, 1024) if min_cells <= 72 * h ** 3 <= max_cells]
     if not hs:
@@ -60,5 +60,5 @@ def poisson_stream(n, rate_per_s=2.0, min_cells=0.5e6, max_cells=20e6, steps_min
         steps = int(rng.integers(steps_min, steps_max + 1))
         storage = str(rng.choice(storages))
         re = float(rng.choice(re_taus))
-        jobs.append(Job(t, channel_case(h, re, storage, seed=i, n_modes=n_modes), steps))
+        jobs.append(Job(t, channel_case(h, re, storage, seed=i, n_modes=n_modes, streaming=streaming), steps))
     return jobs
