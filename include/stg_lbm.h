@@ -206,7 +206,11 @@ int stg_lbm_reset_stats(stg_lbm *h);
 
 /* Copy the populations (storage format g_i = f_i - w_i, 19*nx*ny*nz elements
  * of 4 or 2 bytes, layout f[i][z][y][x]) to or from host memory owned by the
- * caller; both wait for the handle's stream.  set_state also sets the step
+ * caller; both wait for the handle's stream.  The host copy is always the
+ * canonical state: the post-collision populations f*_i of the last step, not
+ * yet streamed, population i of cell x in slot i of x (what the two-lattice
+ * scheme stores); for an in-place lattice the library converts from and to
+ * its arrangement of the current step parity on the host.  set_state also sets the step
  * counter to `step` (>= 0), restarts the temporal filter and takes the state's
  * mass as the reference of the mass check.  `bytes` must equal the state
  * size.  Errors: STG_ERR_INVALID (NULL, size mismatch, negative step, a
@@ -225,9 +229,12 @@ int stg_lbm_checkpoint_bytes(const stg_lbm *h, size_t *bytes);
 int stg_lbm_save(stg_lbm *h, void *host, size_t bytes);
 int stg_lbm_load(stg_lbm *h, const void *host, size_t bytes);
 
-/* Copy a sub-block of the current populations (storage format) to host
- * memory: cells x0..x0+bx-1, y0.., z0.., layout [19][bz][by][bx].  The block
- * must lie inside the lattice.  Errors: STG_ERR_INVALID, STG_ERR_CUDA. */
+/* Copy a sub-block of the current populations (storage format, canonical
+ * arrangement as for stg_lbm_get_state) to host memory: cells x0..x0+bx-1,
+ * y0.., z0.., layout [19][bz][by][bx].  The block must lie inside the lattice.
+ * An in-place lattice gathers the block on the device into a temporary buffer
+ * (cudaMalloc'ed and freed by the call).  Errors: STG_ERR_INVALID,
+ * STG_ERR_CUDA. */
 int stg_lbm_get_block(stg_lbm *h, int32_t x0, int32_t y0, int32_t z0, int32_t bx, int32_t by, int32_t bz,
                       void *host);
 
@@ -240,7 +247,12 @@ int stg_lbm_get_inlet(stg_lbm *h, float *host_u);
 /* Device pointer of the current populations and the inlet plane of the last
  * completed step (valid until the next step / destroy; owned by the library,
  * never freed by the caller); for zero-copy inspection, ordered on the
- * handle's stream.  Either output may be NULL.  Errors: STG_ERR_INVALID. */
+ * handle's stream.  Either output may be NULL.  Two lattices: the canonical
+ * arrangement f[i][z][y][x].  In place: the lattice's own arrangement after t
+ * completed steps -- t even: f*_i of cell x in slot opp(i) of x; t odd: in slot
+ * i of cell x + c_i, or in slot opp(i) of x when x + c_i lies outside the
+ * lattice (a wall in y, the open ends in x); any order-free reduction (such as
+ * the mass) is the same in every arrangement.  Errors: STG_ERR_INVALID. */
 int stg_lbm_device_state(stg_lbm *h, void **pops, float **inlet_u);
 
 /* Derived setup scalars and the device memory held (stg_info).
@@ -287,7 +299,10 @@ int stg_lbm_step_probed(stg_lbm *h, int64_t n, float *u_host);
  * warm-up pass), keep the fastest and store it in *chosen (may be NULL).
  * The trial passes recompute the next state from the current one without
  * advancing the step counter, the inlet filter or the statistics, so tuning
- * leaves the simulation's results unchanged.  Synchronises the stream. */
+ * leaves the simulation's results unchanged.  An in-place lattice's trial
+ * passes update the lattice itself: its populations and step counters are
+ * copied to host memory first and put back afterwards.  Synchronises the
+ * stream. */
 int stg_lbm_autotune(stg_lbm *h, int32_t trial_passes, stg_tile *chosen);
 
 /* Release everything the handle owns (NULL-safe).  Synchronises its stream. */
