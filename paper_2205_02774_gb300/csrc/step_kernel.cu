@@ -6,6 +6,7 @@
 #include "d3q19.cuh"
 #include "internal.h"
 #include "lbm_cell.cuh"
+#include "reduce.cuh"
 
 namespace stg {
 
@@ -133,7 +134,7 @@ template <typename S>
 __global__ void __launch_bounds__(MASS_THREADS) mass_kernel(const MassArgs a)
 {
     const S *src = static_cast<const S *>(a.src);
-    __shared__ double rd[MASS_THREADS];
+    __shared__ double ws[MASS_THREADS / 32];
     __shared__ int s_last;
     double acc = 0.0;
     for (size_t c = blockIdx.x * (size_t)MASS_THREADS + threadIdx.x; c < a.P; c += (size_t)gridDim.x * MASS_THREADS) {
@@ -143,14 +144,9 @@ __global__ void __launch_bounds__(MASS_THREADS) mass_kernel(const MassArgs a)
         acc += (double)r;
     }
     const int tid = threadIdx.x;
-    rd[tid] = acc;
-    __syncthreads();
-    for (int off = MASS_THREADS / 2; off > 0; off >>= 1) {
-        if (tid < off) rd[tid] += rd[tid + off];
-        __syncthreads();
-    }
+    const double bs = block_sum<MASS_THREADS>(acc, ws);
     if (tid == 0) {
-        a.partial[blockIdx.x] = rd[0];
+        a.partial[blockIdx.x] = bs;
         __threadfence();
         s_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
     }
@@ -158,14 +154,9 @@ __global__ void __launch_bounds__(MASS_THREADS) mass_kernel(const MassArgs a)
     if (s_last) {
         double v = 0.0;
         for (unsigned k = tid; k < gridDim.x; k += MASS_THREADS) v += __ldcg(a.partial + k);
-        rd[tid] = v;
-        __syncthreads();
-        for (int off = MASS_THREADS / 2; off > 0; off >>= 1) {
-            if (tid < off) rd[tid] += rd[tid + off];
-            __syncthreads();
-        }
+        const double tot = block_sum<MASS_THREADS>(v, ws);
         if (tid == 0) {
-            a.out[0] = rd[0] + (double)a.P;
+            a.out[0] = tot + (double)a.P;
             *a.counter = 0u;
         }
     }

@@ -57,6 +57,7 @@ def _domain(capi, **kw):
     d.bc_y = kw.get("bc_y", 0)
     d.tau0 = kw.get("tau0", 0.6)
     d.c_smag = kw.get("c_smag", 0.01)
+    d.streaming = kw.get("streaming", 0)
     return d
 
 
@@ -69,6 +70,10 @@ def _domain(capi, **kw):
     (dict(bc_x=0, nx=2), "nx >= 3"),
     (dict(bc_x=0), "RANS profile"),
     (dict(nx=2048, ny=2048, nz=1024), "2^31"),
+    (dict(streaming=5), "bad streaming"),
+    (dict(streaming=1, nx=7), "in-place streaming"),        # odd nx
+    (dict(streaming=1, nx=2), "in-place streaming"),        # nx < 4
+    (dict(streaming=1, nx=2048, ny=1024, nz=128), "in-place streaming"),  # 19 nx ny nz >= 2^32
 ])
 def test_create_rejects_bad_arguments(capi, kw, msg):
     d = _domain(capi, **kw)
@@ -95,3 +100,21 @@ def test_create_rejects_bad_profile(capi):
     with pytest.raises(capi.StgError) as e:
         capi.stg_lbm_create(d, r, prm, 0)
     assert e.value.code == capi.STG_ERR_INVALID and "y_c" in str(e.value)
+
+
+@pytest.mark.parametrize("kw", [dict(storage=2), dict(streaming=1), dict(storage=2, streaming=1, nx=4)])
+def test_create_accepts_stochastic_rounding_and_in_place(capi, kw):
+    """The binary16 storage by stochastic rounding and the in-place scheme pass
+    the argument checks (without a GPU the call then fails in CUDA, not in
+    validation)."""
+    d = _domain(capi, **kw)
+    try:
+        h = capi.stg_lbm_create(d, None, None, 0)
+    except capi.StgError as e:
+        assert e.code == capi.STG_ERR_CUDA, str(e)
+    else:
+        capi.stg_lbm_destroy(h)
+
+
+def test_reset_stats_rejects_null(capi):
+    assert capi.lib().stg_lbm_reset_stats(None) == capi.STG_ERR_INVALID

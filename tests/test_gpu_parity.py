@@ -225,3 +225,31 @@ def test_full_size_sampled_cells(name, storage):
         assert worst <= 0
     st = gpu.stats()
     assert st["rc"] == 0 and math.isfinite(st["mass"])
+
+
+def test_reset_stats_restarts_the_sums():
+    """stg_lbm_reset_stats: sums and sample count restart at the current step
+    (Sec. V statistics over a chosen time window); the populations and the
+    inlet are untouched, so the restarted sums are the full run's sums minus
+    those at the restart."""
+    from paper_2205_02774_gb300.channel import Channel
+    c = SMALL.with_(nx=64, ny=16, nz=12)
+    a = Channel.from_case(c)
+    a.step(13)
+    s13 = a.stats()
+    a.step(39)
+    full = a.stats()
+    fa = a.get_state()
+    a.close()
+    b = Channel.from_case(c)
+    b.step(13)
+    b.reset_stats()
+    st0 = b.stats()
+    assert st0["n_samples"] == 0 and not st0["mean_sum"].any() and not st0["rey_sum"].any()
+    b.step(39)
+    st = b.stats()
+    assert np.array_equal(b.get_state(), fa)
+    b.close()
+    assert st["n_samples"] == full["n_samples"] - s13["n_samples"] == 52 // 10 - 13 // 10
+    for k in ("mean_sum", "rey_sum"):
+        np.testing.assert_allclose(st[k], full[k] - s13[k], rtol=0, atol=1e-12 * np.abs(full[k]).max())
