@@ -151,6 +151,39 @@ struct Interp {
     }
 };
 
+// A fraction of a turn, f in [0, 1), as a Q0.64 fixed-point number.
+uint64_t turns_q64(double f)
+{
+    f -= std::floor(f);
+    const double hi = std::floor(std::ldexp(f, 32));
+    const double lo = std::floor(std::ldexp(std::ldexp(f, 32) - hi, 32));
+    return ((uint64_t)hi << 32) | (uint64_t)lo;
+}
+
+// Modified von Karman spectrum of eq. (qn) (Shur et al.'s form, cited by the
+// paper):
+//   E(k) = (k/k_e)^4 [1 + 2.4 (k/k_e)^2]^(-17/6) exp(-(12 k/k_eta)^2)
+//          exp(-(4 max(k - 0.9 k_cut, 0)/k_cut)^3),
+// k_e = 2 pi/l_e, k_eta = 2 pi/l_eta, k_cut = 2 pi/l_cut; l_e <= 0 gives 0,
+// l_eta <= 0 and l_cut <= 0 switch their factor off.
+double vk_spectrum(double k, double le, double leta, double lcut)
+{
+    if (le <= 0.0) return 0.0;
+    const double r = k * le / (2.0 * kPi);  // k / k_e
+    const double r2 = r * r;
+    double e = r2 * r2 * std::pow(1.0 + 2.4 * r2, -17.0 / 6.0);
+    if (leta > 0.0) {
+        const double g = 12.0 * k * leta / (2.0 * kPi);  // 12 k / k_eta
+        e *= std::exp(-g * g);
+    }
+    if (lcut > 0.0) {
+        const double kc = 2.0 * kPi / lcut;
+        const double hh = 4.0 * std::max(k - 0.9 * kc, 0.0) / kc;
+        e *= std::exp(-hh * hh * hh);
+    }
+    return e;
+}
+
 double wrap2pi(double v)
 {
     v = std::fmod(v, 2.0 * kPi);
@@ -248,42 +281,56 @@ int build_inlet(stg_lbm *h, const stg_rans_profile *r, uint64_t seed)
     h->a_filter = h->p.T_filter > 0.0 ? (float)std::exp(-1.0 / h->p.T_filter) : 0.0f;
     h->info.a_filter = h->a_filter;
 
+    // mode amplitudes sqrt(6 q^n(y_j)), eq. (qn), per inlet node, FP64 on the
+    // host (terms added in mode order)
+    std::vector<float> SQ((size_t)std::max(N, 1) * ny, 0.0f);
+    {
+        std::vector<double> e(std::max(N, 1));
+        for (int j = 0; j < ny; ++j) {
+            double total = 0.0;
+            for (int n = 0; n < N; ++n) {
+                e[n] = vk_spectrum(kn[n], le[j], leta[j], lcut[j]) * dk[n];
+                total += e[n];
+            }
+            for (int n = 0; n < N; ++n) SQ[(size_t)n * ny + j] = total > 0.0 ? (float)std::sqrt(6.0 * e[n] / total) : 0.0f;
+        }
+    }
+    // time part of the phase, phi^n + omega^n t, as Q0.64 fractions of a turn:
+    // the device adds them in wrapping 64-bit integer arithmetic (exact modulo a
+    // turn), so no floating point grows with the step count
+    std::vector<unsigned long long> phq(std::max(N, 1), 0ull), omq(std::max(N, 1), 0ull);
+    for (int n = 0; n < N; ++n) {
+        phq[n] = turns_q64(phi[n] / (2.0 * kPi));
+        omq[n] = turns_q64(omg[n] / (2.0 * kPi));
+    }
+
     // device tables
     const size_t Nn = (size_t)std::max(N, 1);
     h->A = (float *)dalloc(h, sizeof(float) * Nn * ny);
     h->B = (float *)dalloc(h, sizeof(float) * Nn * nz);
     h->SQ = (float *)dalloc(h, sizeof(float) * Nn * ny);
     h->sig = (float *)dalloc(h, sizeof(float) * 3 * Nn);
-    h->phi = (double *)dalloc(h, sizeof(double) * Nn);
-    h->omg = (double *)dalloc(h, sizeof(double) * Nn);
+    h->phq = (unsigned long long *)dalloc(h, sizeof(unsigned long long) * Nn);
+    h->omq = (unsigned long long *)dalloc(h, sizeof(unsigned long long) * Nn);
     h->a6 = (float *)dalloc(h, sizeof(float) * 6 * ny);
     h->u_int = (float *)dalloc(h, sizeof(float) * ny);
     double *dR6 = (double *)dalloc(h, sizeof(double) * 6 * ny);
-    double *dle = (double *)dalloc(h, sizeof(double) * 3 * ny);
-    double *dkn = (double *)dalloc(h, sizeof(double) * 2 * Nn);
-    if (!h->A || !h->B || !h->SQ || !h->sig || !h->phi || !h->omg || !h->a6 || !h->u_int || !dR6 || !dle || !dkn)
+    if (!h->A || !h->B || !h->SQ || !h->sig || !h->phq || !h->omq || !h->a6 || !h->u_int || !dR6)
         return fail(h, STG_ERR_NOMEM, "device allocation of the inlet tables failed");
     std::vector<float> uf(ny);
     for (int j = 0; j < ny; ++j) uf[j] = (float)u_int[j];
-    std::vector<double> lens(3 * (size_t)ny);
-    std::copy(le.begin(), le.end(), lens.begin());
-    std::copy(leta.begin(), leta.end(), lens.begin() + ny);
-    std::copy(lcut.begin(), lcut.end(), lens.begin() + 2 * ny);
     CK(cudaMemcpy(h->u_int, uf.data(), sizeof(float) * ny, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(dR6, R6.data(), sizeof(double) * 6 * ny, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(dle, lens.data(), sizeof(double) * 3 * ny, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->SQ, SQ.data(), sizeof(float) * SQ.size(), cudaMemcpyHostToDevice));
     if (N > 0) {
-        std::vector<double> kd(2 * (size_t)N);
-        std::copy(kn.begin(), kn.end(), kd.begin());
-        std::copy(dk.begin(), dk.end(), kd.begin() + N);
-        CK(cudaMemcpy(dkn, kd.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(h->A, A.data(), sizeof(float) * A.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(h->B, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(h->sig, sig.data(), sizeof(float) * sig.size(), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(h->phi, phi.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(h->omg, omg.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->phq, phq.data(), sizeof(unsigned long long) * N, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->omq, omq.data(), sizeof(unsigned long long) * N, cudaMemcpyHostToDevice));
     }
-    CK(stg::launch_setup_nodes(ny, N, dR6, dle, dle + ny, dle + 2 * ny, dkn, dkn + Nn, h->a6, h->SQ, h->stream));
+    // FP64 Cholesky of the Reynolds stress on the device (setup only)
+    CK(stg::launch_setup_nodes(ny, dR6, h->a6, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return STG_OK;
 }
@@ -365,8 +412,8 @@ stg::InletArgs inlet_args(const stg_lbm *h, int parity)
     a.B = h->B;
     a.SQ = h->SQ;
     a.sig = h->sig;
-    a.phi = h->phi;
-    a.omg = h->omg;
+    a.phq = h->phq;
+    a.omq = h->omq;
     a.a6 = h->a6;
     a.u_int = h->u_int;
     a.a_filter = h->a_filter;
@@ -432,6 +479,9 @@ int capture(stg_lbm *h, int p0, int steps, int single_stats, cudaGraphExec_t *ou
     e = cudaGraphInstantiate(out, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    // upload now, so that the first replay costs no more than later ones
+    e = cudaGraphUpload(*out, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphUpload");
     return STG_OK;
 }
 
@@ -851,8 +901,9 @@ int stg_lbm_estimate_bytes(const stg_domain *d, const stg_params *p, int64_t *by
         double N = 1.0;
         if (p && p->n_modes > 0) N = p->n_modes;
         else if (p && p->alpha > 0.0) N = std::ceil(std::log(1.5 * std::max(ny, 2.0)) / std::log(1.0 + p->alpha) + 1.0);
+        // A, B, SQ, sigma, the two phase words, a6, u_int, the FP64 stresses
         b += r(4 * N * ny) + r(4 * N * nz) + r(4 * N * ny) + r(12 * N) + 2 * r(8 * N) + r(24 * ny) + r(4 * ny) +
-             r(48 * ny) + r(24 * ny) + r(16 * N);
+             r(48 * ny);
     }
     *bytes = (int64_t)b;
     return STG_OK;

@@ -35,7 +35,7 @@ struct stg_lbm {
     float *probe_buf = nullptr;           // device samples of one step_probed call
     size_t probe_cap = 0;                 // floats in probe_buf
     float *A = nullptr, *B = nullptr, *SQ = nullptr, *sig = nullptr, *a6 = nullptr, *u_int = nullptr;
-    double *phi = nullptr, *omg = nullptr;
+    unsigned long long *phq = nullptr, *omq = nullptr;  // phi^n and omega^n as Q0.64 fractions of a turn
     int N = 0;
     float a_filter = 0.f;
     stg::StepCtl *ctl = nullptr;

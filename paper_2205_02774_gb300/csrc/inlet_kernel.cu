@@ -9,9 +9,10 @@
 //   u_bc = u_int(j) e_x + u_f                                               eqs. (u_phys), (u_transfer)
 // The phase is split into three parts each already reduced to [0, 2 pi):
 // the y part and the z part (tables built in FP64 on the host) and the time
-// part phi^n + omega^n t (evaluated in FP64 per block); their FP32 sum is
-// below 6 pi whatever the step count and is reduced to [-pi, pi] before the
-// cosine.
+// part phi^n + omega^n t, kept as Q0.64 fractions of a turn and advanced by
+// wrapping 64-bit integer arithmetic (a phase accumulator: exact modulo a
+// turn for any step count, no floating point); their FP32 sum is below 6 pi
+// and is reduced to [-pi, pi] before the cosine.
 //
 // Work split: a block covers 32 consecutive j (one per lane) by 8 span nodes
 // k; its 8 warps are 4 pairs of span nodes times 2 halves of the mode sum
@@ -38,9 +39,12 @@ constexpr int INLET_H = 2;       // halves of the mode sum
 constexpr int INLET_WARPS = INLET_KG * INLET_H;
 constexpr int INLET_K = INLET_KPT * INLET_KG;  // span nodes per block
 constexpr int INLET_CHUNK = 128; // modes staged per pass through shared memory
-constexpr double TWO_PI = 6.283185307179586476925286766559;
 
-__global__ void __launch_bounds__(INLET_J *INLET_WARPS) stg_inlet_kernel(const InletArgs a)
+// At least 4 blocks per SM caps the kernel at 64 registers, which it fits without
+// spilling; left to itself ptxas aims at the 5 blocks the shared memory allows and
+// spills to a stack frame, and with local memory the kernel no longer ran beside
+// the interior pass (0.75 ms more per step on 1536x256x384 in FP32).
+__global__ void __launch_bounds__(INLET_J * INLET_WARPS, 4) stg_inlet_kernel(const InletArgs a)
 {
     __shared__ float4 ts[INLET_CHUNK];           // (time phase, sigma_x, sigma_y, sigma_z) per mode
     __shared__ float2 bz[INLET_CHUNK][INLET_KG]; // z parts of the block's span nodes per mode
@@ -65,10 +69,10 @@ __global__ void __launch_bounds__(INLET_J *INLET_WARPS) stg_inlet_kernel(const I
         __syncthreads();  // the previous chunk is consumed
         for (int m = tid; m < cn; m += INLET_J * INLET_WARPS) {
             const int n = n0 + m;
-            // time part of the phase, phi^n + omega^n t, reduced to [0, 2 pi) in FP64
-            double th = a.phi[n] + a.omg[n] * (double)t;
-            th -= TWO_PI * floor(th * (1.0 / TWO_PI));  // within a few ulp of [0, 2 pi)
-            ts[m] = make_float4((float)th, a.sig[3 * n + 0], a.sig[3 * n + 1], a.sig[3 * n + 2]);
+            // time part of the phase in turns: phi^n + omega^n t modulo one turn
+            const unsigned long long q = a.phq[n] + a.omq[n] * (unsigned long long)t;
+            const float th = (float)(unsigned)(q >> 32) * 1.4629180792671596e-09f;  // 2 pi / 2^32
+            ts[m] = make_float4(th, a.sig[3 * n + 0], a.sig[3 * n + 1], a.sig[3 * n + 2]);
         }
         for (int e = tid; e < cn * INLET_K; e += INLET_J * INLET_WARPS) {
             const int m = e / INLET_K, kk = e % INLET_K;
@@ -148,72 +152,26 @@ cudaError_t launch_inlet(const InletArgs &a, cudaStream_t s)
 // ---------------------------------------------------------------------------
 // FP64 setup per inlet node j: Cholesky factor of the lattice-unit Reynolds
 // stress (eq. cholesky; a negative radicand counts as zero, a zero pivot
-// zeroes the column) and the mode weights sqrt(6 q^n) from the modified von
-// Karman spectrum (eq. qn; Shur et al.'s form, cited by the paper):
-//   E(k) = (k/k_e)^4 [1 + 2.4 (k/k_e)^2]^(-17/6) exp(-(12 k/k_eta)^2)
-//          exp(-(4 max(k - 0.9 k_cut, 0)/k_cut)^3).
-__device__ double vk_spectrum(double k, double le, double leta, double lcut)
+// zeroes the column).  The mode amplitudes are built on the host.
+__global__ void setup_nodes_kernel(int ny, const double *R6, float *a6)
 {
-    if (le <= 0.0) return 0.0;
-    const double r = k * le / TWO_PI;  // k / k_e
-    const double r2 = r * r;
-    double e = r2 * r2 * pow(1.0 + 2.4 * r2, -17.0 / 6.0);
-    if (leta > 0.0) {
-        const double g = 12.0 * k * leta / TWO_PI;  // 12 k / k_eta
-        e *= exp(-g * g);
-    }
-    if (lcut > 0.0) {
-        const double kc = TWO_PI / lcut;
-        const double h = 4.0 * fmax(k - 0.9 * kc, 0.0) / kc;
-        e *= exp(-h * h * h);
-    }
-    return e;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ny) return;
+    const double *R = R6 + 6 * j;  // 11 22 33 12 13 23
+    const double l11 = sqrt(fmax(R[0], 0.0));
+    const double l21 = l11 > 0.0 ? R[3] / l11 : 0.0;
+    const double l31 = l11 > 0.0 ? R[4] / l11 : 0.0;
+    const double l22 = sqrt(fmax(R[1] - l21 * l21, 0.0));
+    const double l32 = l22 > 0.0 ? (R[5] - l21 * l31) / l22 : 0.0;
+    const double l33 = sqrt(fmax(R[2] - l31 * l31 - l32 * l32, 0.0));
+    float *o = a6 + 6 * j;
+    o[0] = (float)l11; o[1] = (float)l21; o[2] = (float)l22;
+    o[3] = (float)l31; o[4] = (float)l32; o[5] = (float)l33;
 }
 
-// One block per inlet node j; its threads share the mode sum (FP64, fixed
-// reduction order).
-constexpr int SETUP_THREADS = 128;
-
-__global__ void __launch_bounds__(SETUP_THREADS) setup_nodes_kernel(int ny, int N, const double *R6, const double *le,
-                                                                     const double *leta, const double *lcut,
-                                                                     const double *kn, const double *dk, float *a6,
-                                                                     float *SQ)
+cudaError_t launch_setup_nodes(int ny, const double *R6, float *a6, cudaStream_t s)
 {
-    __shared__ double red[SETUP_THREADS];
-    const int j = blockIdx.x;
-    if (threadIdx.x == 0) {
-        const double *R = R6 + 6 * j;  // 11 22 33 12 13 23
-        const double l11 = sqrt(fmax(R[0], 0.0));
-        const double l21 = l11 > 0.0 ? R[3] / l11 : 0.0;
-        const double l31 = l11 > 0.0 ? R[4] / l11 : 0.0;
-        const double l22 = sqrt(fmax(R[1] - l21 * l21, 0.0));
-        const double l32 = l22 > 0.0 ? (R[5] - l21 * l31) / l22 : 0.0;
-        const double l33 = sqrt(fmax(R[2] - l31 * l31 - l32 * l32, 0.0));
-        float *o = a6 + 6 * j;
-        o[0] = (float)l11; o[1] = (float)l21; o[2] = (float)l22;
-        o[3] = (float)l31; o[4] = (float)l32; o[5] = (float)l33;
-    }
-    const double lej = le[j], letaj = leta[j], lcutj = lcut[j];
-    double acc = 0.0;
-    for (int n = threadIdx.x; n < N; n += SETUP_THREADS) acc += vk_spectrum(kn[n], lej, letaj, lcutj) * dk[n];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int off = SETUP_THREADS / 2; off > 0; off >>= 1) {
-        if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
-        __syncthreads();
-    }
-    const double total = red[0];
-    for (int n = threadIdx.x; n < N; n += SETUP_THREADS) {
-        const double q = total > 0.0 ? vk_spectrum(kn[n], lej, letaj, lcutj) * dk[n] / total : 0.0;
-        SQ[(size_t)n * ny + j] = (float)sqrt(6.0 * q);
-    }
-}
-
-cudaError_t launch_setup_nodes(int ny, int N, const double *R6, const double *le, const double *leta,
-                               const double *lcut, const double *kn, const double *dk, float *a6, float *SQ,
-                               cudaStream_t s)
-{
-    setup_nodes_kernel<<<ny, SETUP_THREADS, 0, s>>>(ny, N, R6, le, leta, lcut, kn, dk, a6, SQ);
+    setup_nodes_kernel<<<(ny + 127) / 128, 128, 0, s>>>(ny, R6, a6);
     return cudaGetLastError();
 }
 

@@ -65,8 +65,8 @@ struct InletArgs {
     const float *B;       // [N][nz]  k^n d^n_z k       mod 2 pi
     const float *SQ;      // [N][ny]  sqrt(6 q^n(y_j))
     const float *sig;     // [N][3]   sigma^n
-    const double *phi;    // [N]      phi^n
-    const double *omg;    // [N]      phase advance per step, -2 pi d^n_x U_b / max l_e
+    const unsigned long long *phq;  // [N] phi^n / (2 pi) as a Q0.64 fraction of a turn
+    const unsigned long long *omq;  // [N] phase advance per step, -d^n_x U_b / max l_e turns, Q0.64
     const float *a6;      // [ny][6]  Cholesky factor a11 a21 a22 a31 a32 a33
     const float *u_int;   // [ny]     interpolated mean streamwise velocity
     float a_filter;
@@ -94,9 +94,8 @@ cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stat
                         cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join,
                         const InletArgs *inlet = nullptr);
 cudaError_t launch_inlet(const InletArgs &a, cudaStream_t s);
-cudaError_t launch_setup_nodes(int ny, int N, const double *R6, const double *le, const double *leta,
-                               const double *lcut, const double *kn, const double *dk, float *a6,
-                               float *SQ, cudaStream_t s);
+// FP64 Cholesky factor of the lattice-unit Reynolds stress per inlet node (setup)
+cudaError_t launch_setup_nodes(int ny, const double *R6, float *a6, cudaStream_t s);
 // swap: store population i in slot opp(i) (the in-place layout before a step of even index)
 cudaError_t launch_init_equilibrium(void *dst, int storage, int nx, int ny, int nz, const float *u_int, int swap,
                                     cudaStream_t s);

@@ -253,3 +253,24 @@ def test_reset_stats_restarts_the_sums():
     assert st["n_samples"] == full["n_samples"] - s13["n_samples"] == 52 // 10 - 13 // 10
     for k in ("mean_sum", "rey_sum"):
         np.testing.assert_allclose(st[k], full[k] - s13[k], rtol=0, atol=1e-12 * np.abs(full[k]).max())
+
+
+@pytest.mark.parametrize("T", [1, 4097, 12_345_678])
+def test_inlet_plane_at_a_late_step(T):
+    """The time phase phi^n + omega^n t of eq. (psu) at a large step index:
+    after set_state(..., T) and one step, the inlet plane of step T equals the
+    oracle's generator evaluated at t = T (filter off), to 1e-5 of max |u|.
+    The phase grows like omega t (about 2e5 rad at T ~ 1e7 here), so this
+    checks that the device keeps it exact modulo a turn."""
+    c = SMALL.with_(stats_every=0, t_filter=0.0)
+    gpu, orc = pair(c)
+    gpu.set_state(gpu.get_state(), T)
+    gpu.step(1)
+    u_g = gpu.inlet()
+    tab = orc.tables()
+    u_o = np.zeros_like(u_g, dtype=np.float64)
+    for k in range(c.nz):
+        for j in range(c.ny):
+            u_o[:, k, j] = orc.stg_raw(T, j, k)
+            u_o[0, k, j] += tab["u_int"][j]
+    assert np.abs(u_g - u_o).max() <= 1e-5 * np.abs(u_o).max()

@@ -19,7 +19,7 @@ def test_poisson_stream_recipe():
         assert (j.case.nx, j.case.ny, j.case.nz) == (12 * h, 2 * h, 3 * h)
         assert 0.5e6 <= j.case.cells <= 20e6
         assert 1000 <= j.steps <= 20000
-        assert j.case.storage in ("fp32", "fp16s") and j.case.re_tau in (180.0, 395.0)
+        assert j.case.storage in ("fp32", "fp16sr") and j.case.re_tau in (180.0, 395.0)
     assert [j.case.seed for j in jobs] == list(range(500))
     again = poisson_stream(500, rate_per_s=2.0, seed=7)
     assert [(j.arrival_s, j.case, j.steps) for j in jobs] == [(j.arrival_s, j.case, j.steps) for j in again]

@@ -10,7 +10,8 @@ and seed.  Two recipes:
 * poisson_stream(n, rate, ...): n jobs arriving as a Poisson process; h is
   uniform on the integers whose lattice has between min_cells and max_cells
   cells, steps uniform in [steps_min, steps_max], storage uniform on
-  {fp32, fp16s}, Re_tau uniform on {180, 395}, seed = job id.
+  {fp32, fp16sr} (binary16 written by stochastic rounding), Re_tau uniform
+  on {180, 395}, seed = job id.
 
 Only random draws live here; no step of the method is evaluated.
 """
@@ -47,7 +48,7 @@ def ensemble(n, heights=(16, 24, 32, 48, 64), re_taus=(180, 395), steps=5000, dr
 
 
 def poisson_stream(n, rate_per_s=2.0, min_cells=0.5e6, max_cells=20e6, steps_min=1000, steps_max=20000,
-                   storages=("fp32", "fp16s"), re_taus=(180, 395), seed=7, n_modes=200, streaming="pull"):
+                   storages=("fp32", "fp16sr"), re_taus=(180, 395), seed=7, n_modes=200, streaming="pull"):
     rng = np.random.default_rng(seed)
     hs = [h for h in range(2, 1024) if min_cells <= 72 * h ** 3 <= max_cells]
     if not hs:
