@@ -57,7 +57,7 @@ def _kernel_hash():
     """Hash of the step kernels' source with comments and white space removed
     (a comment edit does not change the kernel whose counters were taken)."""
     h = hashlib.sha256()
-    for f in ("step_kernel.cu", "step_kernel.cuh", "d3q19.cuh", "internal.h", "lbm_cell.cuh", "reduce.cuh"):
+    for f in ("step_kernel.cu", "step_kernel.cuh", "d3q19.cuh", "internal.h", "lbm_cell.cuh", "lbm_pair.cuh", "reduce.cuh"):
         with open(os.path.join(ROOT, "paper_2205_02774_gb300", "csrc", f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)

@@ -28,10 +28,26 @@ struct Pop<__half> {
     static __device__ __forceinline__ void st(__half *p, float g) { __stcs(p, __float2half_rn(g)); }
 };
 
+// Every multiply-add below is written out: a product that feeds an addition
+// is either fused by an explicit fmaf or formed by __fmul_rn, which the
+// compiler may not fuse.  Left to itself the compiler contracts such pairs
+// differently in different kernel instances, and the instances that share
+// this code (tiles, sampling and plain steps, both streaming schemes) must
+// round every cell alike.
+
+// c_i . u for a lattice direction (components in {-1, 0, 1}), no products
+__device__ __forceinline__ float cdot(int cx, int cy, int cz, float ux, float uy, float uz)
+{
+    float r = cx > 0 ? ux : (cx < 0 ? -ux : 0.f);
+    if (cy) r = cx ? (cy > 0 ? r + uy : r - uy) : (cy > 0 ? uy : -uy);
+    if (cz) r = (cx || cy) ? (cz > 0 ? r + uz : r - uz) : (cz > 0 ? uz : -uz);
+    return r;
+}
+
 // shifted equilibrium g^eq_i = f^eq_i - w_i = w_i [drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)]
 __device__ __forceinline__ float geq(float w, float drho, float rho, float cu, float uu)
 {
-    return w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+    return __fmul_rn(w, fmaf(rho, fmaf(cu, fmaf(4.5f, cu, 3.0f), -1.5f * uu), drho));
 }
 
 // Regularized rebuild of a boundary node (eqs. f_i, f_i_neq, pi_neq,
@@ -42,11 +58,11 @@ template <int SGN>
 __device__ __forceinline__ void rebuild(float (&g)[Q], float drho, float ux, float uy, float uz)
 {
     const float rho = 1.0f + drho;
-    const float uu = ux * ux + uy * uy + uz * uz;
+    const float uu = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        if (cx != SGN) g[i] = g[i] - geq(w_of(i), drho, rho, cx * ux + cy * uy + cz * uz, uu);
+        if (cx != SGN) g[i] = g[i] - geq(w_of(i), drho, rho, cdot(cx, cy, cz, ux, uy, uz), uu);
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i)
@@ -65,16 +81,24 @@ __device__ __forceinline__ void rebuild(float (&g)[Q], float drho, float ux, flo
         if (cy * cz) pyz += cy * cz * v;
     }
     // Pi_neq = sum_i Q_i f_i^neq with Q_i = c_i c_i - I/3
-    pxx -= s * (1.0f / 3.0f);
-    pyy -= s * (1.0f / 3.0f);
-    pzz -= s * (1.0f / 3.0f);
-    const float tr3 = (pxx + pyy + pzz) * (1.0f / 3.0f);
+    pxx = fmaf(-1.0f / 3.0f, s, pxx);
+    pyy = fmaf(-1.0f / 3.0f, s, pyy);
+    pzz = fmaf(-1.0f / 3.0f, s, pzz);
+    const float tsum = (pxx + pyy) + pzz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const float cpc = cx * cx * pxx + cy * cy * pyy + cz * cz * pzz
-                        + 2.0f * (cx * cy * pxy + cx * cz * pxz + cy * cz * pyz);
-        g[i] = geq(w_of(i), drho, rho, cx * ux + cy * uy + cz * uz, uu) + 4.5f * w_of(i) * (cpc - tr3);
+        // c.Pi.c = diagonal part + 2 x off-diagonal part (the terms with c_a c_b != 0)
+        float dg = 0.f, od = 0.f;
+        if (cx) dg = pxx;
+        if (cy) dg = cx ? dg + pyy : pyy;
+        if (cz) dg = (cx || cy) ? dg + pzz : pzz;
+        if (cx * cy) od = cx * cy > 0 ? pxy : -pxy;
+        if (cx * cz) od = cx * cz > 0 ? pxz : -pxz;
+        if (cy * cz) od = cy * cz > 0 ? pyz : -pyz;
+        const float cpc = (cx * cy || cx * cz || cy * cz) ? fmaf(2.0f, od, dg) : dg;
+        g[i] = fmaf(4.5f * w_of(i), fmaf(-1.0f / 3.0f, tsum, cpc),
+                    geq(w_of(i), drho, rho, cdot(cx, cy, cz, ux, uy, uz), uu));
     }
 }
 
@@ -129,77 +153,76 @@ __device__ __forceinline__ void collide_sd(float (&g)[Q], const float (&s)[9], c
     }
     const float rho = 1.0f + drho;
     const float irho = 1.0f / rho;
-    const float ux = (FORCE ? jx + 0.5f * Fx : jx) * irho;
-    const float uy = (FORCE ? jy + 0.5f * Fy : jy) * irho;
-    const float uz = (FORCE ? jz + 0.5f * Fz : jz) * irho;
+    const float ux = (FORCE ? fmaf(0.5f, Fx, jx) : jx) * irho;
+    const float uy = (FORCE ? fmaf(0.5f, Fy, jy) : jy) * irho;
+    const float uz = (FORCE ? fmaf(0.5f, Fz, jz) : jz) * irho;
     // Pi_neq = Pi - rho (cs^2 I + u u) = sum c c g - drho/3 I - rho u u
     const float rux = rho * ux, ruy = rho * uy, ruz = rho * uz;
-    const float d3 = drho * (1.0f / 3.0f);
-    const float nxx = pxx - d3 - rux * ux;
-    const float nyy = pyy - d3 - ruy * uy;
-    const float nzz = pzz - d3 - ruz * uz;
-    const float nxy = pxy - rux * uy;
-    const float nxz = pxz - rux * uz;
-    const float nyz = pyz - ruy * uz;
-    const float q2 = nxx * nxx + nyy * nyy + nzz * nzz + 2.0f * (nxy * nxy + nxz * nxz + nyz * nyz);
+    const float nxx = fmaf(-rux, ux, fmaf(-1.0f / 3.0f, drho, pxx));
+    const float nyy = fmaf(-ruy, uy, fmaf(-1.0f / 3.0f, drho, pyy));
+    const float nzz = fmaf(-ruz, uz, fmaf(-1.0f / 3.0f, drho, pzz));
+    const float nxy = fmaf(-rux, uy, pxy);
+    const float nxz = fmaf(-rux, uz, pxz);
+    const float nyz = fmaf(-ruy, uz, pyz);
+    const float q2 = fmaf(2.0f, fmaf(nyz, nyz, fmaf(nxz, nxz, nxy * nxy)), fmaf(nzz, nzz, fmaf(nyy, nyy, nxx * nxx)));
     const float qh = q2 > 0.f ? sqrtf(q2) : 0.f;
     // eq. (tau_eff), c = 1: tau = tau0/2 + sqrt((tau0 rho)^2 + 18 sqrt2 C Q^1/2)/(2 rho)
-    float tau = 0.5f * (tau0 + sqrtf(tau0 * tau0 + kq * qh * irho * irho));
+    float tau = 0.5f * (tau0 + sqrtf(fmaf(kq * qh, irho * irho, tau0 * tau0)));
     if (SP) tau = fmaf(nuf, tau - 0.5f, 0.5f);
     const float om = 1.0f / tau;
-    const float uu = ux * ux + uy * uy + uz * uz;
-    const float kf = FORCE ? (1.0f - 0.5f * om) : 0.f;  // Guo prefactor
-    const float uF = FORCE ? ux * Fx + uy * Fy + uz * Fz : 0.f;
+    const float uu = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
+    const float kf = FORCE ? fmaf(-0.5f, om, 1.0f) : 0.f;  // Guo prefactor
+    const float uF = FORCE ? fmaf(uz, Fz, fmaf(uy, Fy, ux * Fx)) : 0.f;
     float a0, Bx, By, Bz, Axx, Ayy, Azz, Axy, Axz, Ayz, K;
     if (REG) {
         const float km = 1.0f - om;
         const float k45 = 4.5f * km;
-        a0 = drho - 1.5f * rho * uu - 1.5f * km * (nxx + nyy + nzz);
+        a0 = fmaf(-1.5f, fmaf(km, (nxx + nyy) + nzz, rho * uu), drho);
         Bx = 3.0f * rux;
         By = 3.0f * ruy;
         Bz = 3.0f * ruz;
-        Axx = 4.5f * rux * ux + k45 * nxx;
-        Ayy = 4.5f * ruy * uy + k45 * nyy;
-        Azz = 4.5f * ruz * uz + k45 * nzz;
-        Axy = 4.5f * rux * uy + k45 * nxy;
-        Axz = 4.5f * rux * uz + k45 * nxz;
-        Ayz = 4.5f * ruy * uz + k45 * nyz;
+        Axx = fmaf(k45, nxx, (4.5f * rux) * ux);
+        Ayy = fmaf(k45, nyy, (4.5f * ruy) * uy);
+        Azz = fmaf(k45, nzz, (4.5f * ruz) * uz);
+        Axy = fmaf(k45, nxy, (4.5f * rux) * uy);
+        Axz = fmaf(k45, nxz, (4.5f * rux) * uz);
+        Ayz = fmaf(k45, nyz, (4.5f * ruy) * uz);
         K = 0.f;
         if (FORCE) {
             // regularized: the first-order neq part a1 = -F/2 is kept
-            const float kb = 3.0f * kf - 1.5f * km;
-            Bx += kb * Fx;
-            By += kb * Fy;
-            Bz += kb * Fz;
+            const float kb = fmaf(3.0f, kf, -1.5f * km);
+            Bx = fmaf(kb, Fx, Bx);
+            By = fmaf(kb, Fy, By);
+            Bz = fmaf(kb, Fz, Bz);
         }
     } else {
-        a0 = om * (drho - 1.5f * rho * uu);
+        a0 = om * fmaf(-1.5f * rho, uu, drho);
         const float r3 = 3.0f * om, r45 = 4.5f * om;
         Bx = r3 * rux;
         By = r3 * ruy;
         Bz = r3 * ruz;
-        Axx = r45 * rux * ux;
-        Ayy = r45 * ruy * uy;
-        Azz = r45 * ruz * uz;
-        Axy = r45 * rux * uy;
-        Axz = r45 * rux * uz;
-        Ayz = r45 * ruy * uz;
+        Axx = __fmul_rn(r45 * rux, ux);
+        Ayy = __fmul_rn(r45 * ruy, uy);
+        Azz = __fmul_rn(r45 * ruz, uz);
+        Axy = __fmul_rn(r45 * rux, uy);
+        Axz = __fmul_rn(r45 * rux, uz);
+        Ayz = __fmul_rn(r45 * ruy, uz);
         K = 1.0f - om;
         if (FORCE) {
-            Bx += 3.0f * kf * Fx;
-            By += 3.0f * kf * Fy;
-            Bz += 3.0f * kf * Fz;
+            Bx = fmaf(3.0f * kf, Fx, Bx);
+            By = fmaf(3.0f * kf, Fy, By);
+            Bz = fmaf(3.0f * kf, Fz, Bz);
         }
     }
     if (FORCE) {
-        const float k9 = 9.0f * kf;
-        a0 -= 3.0f * kf * uF;
-        Axx += k9 * ux * Fx;
-        Ayy += k9 * uy * Fy;
-        Azz += k9 * uz * Fz;
-        Axy += 0.5f * k9 * (ux * Fy + uy * Fx);
-        Axz += 0.5f * k9 * (ux * Fz + uz * Fx);
-        Ayz += 0.5f * k9 * (uy * Fz + uz * Fy);
+        const float k9 = 9.0f * kf, k45 = 4.5f * kf;
+        a0 = fmaf(-3.0f * kf, uF, a0);
+        Axx = fmaf(k9 * ux, Fx, Axx);
+        Ayy = fmaf(k9 * uy, Fy, Ayy);
+        Azz = fmaf(k9 * uz, Fz, Azz);
+        Axy = fmaf(k45, fmaf(ux, Fy, uy * Fx), Axy);
+        Axz = fmaf(k45, fmaf(ux, Fz, uz * Fx), Axz);
+        Ayz = fmaf(k45, fmaf(uy, Fz, uz * Fy), Ayz);
     }
     constexpr float W0 = 1.0f / 3.0f, W1 = 1.0f / 18.0f, W2 = 1.0f / 36.0f;
     // rest population
@@ -208,26 +231,28 @@ __device__ __forceinline__ void collide_sd(float (&g)[Q], const float (&s)[9], c
     {
         const float w1a0 = W1 * a0;
         const float ex = fmaf(W1, Axx, w1a0), ey = fmaf(W1, Ayy, w1a0), ez = fmaf(W1, Azz, w1a0);
-        const float ox = W1 * Bx, oy = W1 * By, oz = W1 * Bz;
+        const float px = fmaf(W1, Bx, ex), mx = fmaf(-W1, Bx, ex);
+        const float py = fmaf(W1, By, ey), my = fmaf(-W1, By, ey);
+        const float pz = fmaf(W1, Bz, ez), mz = fmaf(-W1, Bz, ez);
         if (REG) {
-            g[1] = ex + ox; g[2] = ex - ox;
-            g[3] = ey + oy; g[4] = ey - oy;
-            g[5] = ez + oz; g[6] = ez - oz;
+            g[1] = px; g[2] = mx;
+            g[3] = py; g[4] = my;
+            g[5] = pz; g[6] = mz;
         } else {
-            g[1] = fmaf(K, g[1], ex + ox); g[2] = fmaf(K, g[2], ex - ox);
-            g[3] = fmaf(K, g[3], ey + oy); g[4] = fmaf(K, g[4], ey - oy);
-            g[5] = fmaf(K, g[5], ez + oz); g[6] = fmaf(K, g[6], ez - oz);
+            g[1] = fmaf(K, g[1], px); g[2] = fmaf(K, g[2], mx);
+            g[3] = fmaf(K, g[3], py); g[4] = fmaf(K, g[4], my);
+            g[5] = fmaf(K, g[5], pz); g[6] = fmaf(K, g[6], mz);
         }
     }
     // edge pairs: (7,8) +-(1,1,0), (9,10) +-(1,-1,0), (11,12) +-(1,0,1), (13,14) +-(1,0,-1),
     //             (15,16) +-(0,1,1), (17,18) +-(0,1,-1)
     {
         const float w2a0 = W2 * a0;
-        const float bx = W2 * Bx, by = W2 * By, bz = W2 * Bz;
-        const float sxy = fmaf(W2, Axx + Ayy, w2a0), txy = (2.0f * W2) * Axy;
-        const float sxz = fmaf(W2, Axx + Azz, w2a0), txz = (2.0f * W2) * Axz;
-        const float syz = fmaf(W2, Ayy + Azz, w2a0), tyz = (2.0f * W2) * Ayz;
-        const float e7 = sxy + txy, e9 = sxy - txy, e11 = sxz + txz, e13 = sxz - txz, e15 = syz + tyz, e17 = syz - tyz;
+        const float bx = __fmul_rn(W2, Bx), by = __fmul_rn(W2, By), bz = __fmul_rn(W2, Bz);
+        const float sxy = fmaf(W2, Axx + Ayy, w2a0), sxz = fmaf(W2, Axx + Azz, w2a0), syz = fmaf(W2, Ayy + Azz, w2a0);
+        const float e7 = fmaf(2.0f * W2, Axy, sxy), e9 = fmaf(-2.0f * W2, Axy, sxy);
+        const float e11 = fmaf(2.0f * W2, Axz, sxz), e13 = fmaf(-2.0f * W2, Axz, sxz);
+        const float e15 = fmaf(2.0f * W2, Ayz, syz), e17 = fmaf(-2.0f * W2, Ayz, syz);
         const float o7 = bx + by, o9 = bx - by, o11 = bx + bz, o13 = bx - bz, o15 = by + bz, o17 = by - bz;
         if (REG) {
             g[7] = e7 + o7; g[8] = e7 - o7;

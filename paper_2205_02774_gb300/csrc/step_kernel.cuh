@@ -41,6 +41,7 @@
 #include "d3q19.cuh"
 #include "internal.h"
 #include "lbm_cell.cuh"
+#include "lbm_pair.cuh"
 #include "reduce.cuh"
 
 namespace stg {
@@ -195,7 +196,7 @@ __device__ __forceinline__ void step_column(const StepArgs &a, int bx, int y)
                             if (cx_of(i) == 0) par += g[i];
                             if (cx_of(i) < 0) lv += g[i];
                         }
-                        const float drb = (par + 2.0f * lv + ubx) / (1.0f - ubx);
+                        const float drb = (fmaf(2.0f, lv, par) + ubx) / (1.0f - ubx);
                         rebuild<1>(g, drb, ubx, uby, ubz);
                     } else {
                         // zero-gradient pressure outlet: rho = 1 and the velocity of the
@@ -286,6 +287,7 @@ struct Vec<float, 2> {
     using raw = float2;
     static __device__ __forceinline__ raw ld(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
     static __device__ __forceinline__ float cell(raw v, int j) { return j ? v.y : v.x; }
+    static __device__ __forceinline__ float2 pair(raw v) { return v; }
     static __device__ __forceinline__ void put(raw &v, int j, float f)
     {
         if (j) v.y = f;
@@ -367,6 +369,14 @@ struct Vec<__half, 2> {
         float f;
         if (j) asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %1; cvt.f32.f16 %0, hi;}" : "=f"(f) : "r"(v));
         else asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %1; cvt.f32.f16 %0, lo;}" : "=f"(f) : "r"(v));
+        return f;
+    }
+    // both halves in FP32 (.x the first cell)
+    static __device__ __forceinline__ float2 pair(raw v)
+    {
+        float2 f;
+        asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %2; cvt.f32.f16 %0, lo; cvt.f32.f16 %1, hi;}"
+            : "=f"(f.x), "=f"(f.y) : "r"(v));
         return f;
     }
     // h_j + c and h_j - c in FP32 with the binary16 half j of the pair as an
@@ -480,6 +490,13 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
     using raw = typename V::raw;
     // binary16 pairs, regularized collision: pair sums by mixed-precision adds
     constexpr bool MIXED = REG && sizeof(S) == 2 && CPL == 2;
+    // binary16 pairs, regularized unforced collision: both cells in packed
+    // FP32 (lbm_pair.cuh) wherever the warp's 64 cells hold no inlet or outlet
+    // node; the warps that do, the other collisions and FP32 storage (whose
+    // step is bound by memory either way) update cell by cell.  A warp's chunk
+    // is the same in every kernel and tile, so each cell always takes the
+    // same form.
+    constexpr bool PACKED = REG && !FORCE && sizeof(S) == 2 && CPL == 2;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int nxy = nx * ny;
     const int lane = threadIdx.x, wi = threadIdx.y;
@@ -496,6 +513,7 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
     // CPL); both are rebuilt here from the values already in registers
     const bool at_inlet = inout && x == 0;
     const bool at_outlet = inout && active && x + CPL == nx;
+    const bool node_warp = inout && (x0 == 0 || x0 + BX * CPL >= nx);
     // y neighbours of this row (YEDGE rows only)
     bool ym_bb = false, yp_bb = false;
     int ym_off = nx, yp_off = -nx;  // element offset of the source row for c_y = +1 / -1 (subtracted)
@@ -573,6 +591,33 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
             else v[i] = V::shift_right(cur, sbase + (rbase + xr), side_r && !(inout && x + CPL == nx));
         }
         const unsigned seed = SR ? sr_seed(here, tmix) : 0u;
+        if (PACKED && !node_warp) {
+            // both cells of the lane at once (packed FP32 pairs)
+            float2 nuf = make_float2(1.0f, 1.0f);
+            if (SP && active) nuf = __ldg(reinterpret_cast<const float2 *>(a.spf + x));
+            const PairMoments m = pair_moments([&](int i) { return V::pair(v[i]); });
+            float2 drho, ux, uy, uz;
+            collide_pair<SP>(m, tau0, kq, nuf, [&](int i, float2 r) {
+                if constexpr (SR) v[i] = V::pack_rs(r.x, r.y, sr_bits(seed, i));
+                else v[i] = V::pack(r.x, r.y);
+            }, drho, ux, uy, uz);
+            if (active) {
+                if (STATS) {
+                    constexpr int L = BX * CPL;
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j) {
+                        float *sp = &sacc[wi][0][CPL * lane + j];
+                        const float vx = j ? ux.y : ux.x, vy = j ? uy.y : uy.x, vz = j ? uz.y : uz.x;
+                        sp[0 * L] += vx; sp[1 * L] += vy; sp[2 * L] += vz;
+                        sp[3 * L] = __fmaf_rn(vx, vx, sp[3 * L]); sp[4 * L] = __fmaf_rn(vy, vy, sp[4 * L]);
+                        sp[5 * L] = __fmaf_rn(vz, vz, sp[5 * L]); sp[6 * L] = __fmaf_rn(vx, vy, sp[6 * L]);
+                        sp[7 * L] = __fmaf_rn(vx, vz, sp[7 * L]); sp[8 * L] = __fmaf_rn(vy, vz, sp[8 * L]);
+                    }
+                }
+                sdr += drho.x;
+                sdr += drho.y;
+            }
+        } else {
         float upx = 0.f, upy = 0.f, upz = 0.f;  // velocity of the lane's previous cell
         float gp[CPL == 2 ? Q : 1];             // first cell's results (pairs)
 #pragma unroll
@@ -593,7 +638,7 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
                         if (cx_of(i) == 0) par += gg[i];
                         if (cx_of(i) < 0) lv += gg[i];
                     }
-                    rebuild<1>(gg, (par + 2.0f * lv + ubx) / (1.0f - ubx), ubx, uby, ubz);
+                    rebuild<1>(gg, (fmaf(2.0f, lv, par) + ubx) / (1.0f - ubx), ubx, uby, ubz);
                 }
                 if (j == CPL - 1 && at_outlet) {
                     // zero-gradient pressure outlet: rho = 1 and the velocity of the
@@ -661,6 +706,7 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
             }
             if (counted) sdr += drho;
         }
+        }
         if (active) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -720,7 +766,9 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
 // count); plain steps use lbm_vec_zc_kernel.
 constexpr int STAT_NW = 4;  // warps (x chunks) per sampling block
 template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP, bool H16, int MODE, bool SR>
-__global__ void __launch_bounds__(BX *STAT_NW, (REG && !FORCE && !YEDGE) ? 8 : 6) lbm_vec_kernel(const StepArgs a)
+// (the wall rows, on the branch beside the interior launch, may take 128
+// registers so that they need no stack frame)
+__global__ void __launch_bounds__(BX *STAT_NW, YEDGE ? 4 : ((REG && !FORCE) ? 8 : 6)) lbm_vec_kernel(const StepArgs a)
 {
     constexpr int CPL = VecOf<S>::CPL;
     __shared__ float sacc[STATS ? STAT_NW : 1][9][BX * CPL];  // per-thread statistics slots
