@@ -716,36 +716,40 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
                 }
                 // the cell's own slot opp(i): the target of every local result,
                 // and of a shifted result whose target lies outside the lattice
-                S *own = reinterpret_cast<S *>(reinterpret_cast<char *>(dbase + here) + (size_t)opp_of(i) * Pb);
+                auto own_slot = [&](int k) {
+                    return reinterpret_cast<S *>(reinterpret_cast<char *>(dbase + here) + (size_t)opp_of(k) * Pb);
+                };
                 if (MODE == AA_LOCAL) {
-                    V::st(own, v[i]);
+                    V::st(own_slot(i), v[i]);
                     continue;
                 }
                 // in place, even steps: result of population i to slot i at x + c_i
                 const int cx = cx_of(i), cz = cz_of(i), cy = cy_of(i);
                 const bool yout = YEDGE && ((cy > 0 && yp_bb) || (cy < 0 && ym_bb));
                 if (yout) {
-                    V::st(own, v[i]);
+                    V::st(own_slot(i), v[i]);
                     continue;
                 }
                 // target row (y + c_y, z + c_z): the source row of population opp(i)
                 const unsigned tz = cz > 0 ? 0u - dzp : (cz < 0 ? 0u - dzm : 0u);
                 const unsigned ty = cy > 0 ? (YEDGE ? 0u - (unsigned)yp_off : nxv) : (cy < 0 ? (YEDGE ? 0u - (unsigned)ym_off : 0u - nxv) : 0u);
                 S *trow = reinterpret_cast<S *>(reinterpret_cast<char *>(dbase + (row0 + tz + ty)) + (size_t)i * Pb);
+                S *tx = trow + x;
                 if (cx == 0) {
-                    V::st(trow + x, v[i]);
+                    V::st(tx, v[i]);
                 } else if (cx < 0) {
-                    // cell x -> x - 1 (outside at the inlet, wraps when x is periodic), cell x + 1 -> x
-                    if (x > 0) V::st1(trow + (x - 1), v[i], 0);
-                    else if (inout) V::st1(own, v[i], 0);
-                    else V::st1(trow + (nx - 1), v[i], 0);
-                    V::st1(trow + (x - 1), v[i], 1);
+                    // cell x + 1 -> x, cell x -> x - 1; the row's first cell
+                    // (lanes with x = 0 only): outside at the inlet (the own slot),
+                    // wraps to x = nx - 1 when x is periodic
+                    V::st1(tx - 1, v[i], 1);
+                    if (x > 0) V::st1(tx - 1, v[i], 0);
+                    else V::st1(inout ? own_slot(i) : tx + (nx - 1), v[i], 0);
                 } else {
-                    // cell x -> x + 1, cell x + 1 -> x + 2 (outside at the outlet, wraps when periodic)
-                    V::st1(trow + (x + 1), v[i], 0);
-                    if (x + 2 < nx) V::st1(trow + (x + 1), v[i], 1);
-                    else if (inout) V::st1(own, v[i], 1);
-                    else V::st1(trow - 1, v[i], 1);
+                    // cell x -> x + 1, cell x + 1 -> x + 2; the row's last cell
+                    // (lanes with x = nx - 2 only): outside at the outlet, wraps to 0
+                    V::st1(tx + 1, v[i], 0);
+                    if (x + 2 < nx) V::st1(tx + 1, v[i], 1);
+                    else V::st1(inout ? own_slot(i) : tx - (x + 1), v[i], 1);
                 }
             }
         }
