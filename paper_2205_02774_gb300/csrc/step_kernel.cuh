@@ -287,7 +287,8 @@ struct Vec<float, 2> {
     using raw = float2;
     static __device__ __forceinline__ raw ld(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
     static __device__ __forceinline__ float cell(raw v, int j) { return j ? v.y : v.x; }
-    static __device__ __forceinline__ float2 pair(raw v) { return v; }
+    static __device__ __forceinline__ float2 pair(raw v, int = 0) { return v; }
+    static __device__ __forceinline__ void set_pair(raw &v, int, float lo, float hi) { v = make_float2(lo, hi); }
     static __device__ __forceinline__ void put(raw &v, int j, float f)
     {
         if (j) v.y = f;
@@ -312,43 +313,6 @@ struct Vec<float, 2> {
     }
 };
 
-__device__ __forceinline__ float h2f(unsigned v, int hi)
-{
-    return __half2float(__ushort_as_half((unsigned short)(hi ? v >> 16 : v & 0xffffu)));
-}
-__device__ __forceinline__ unsigned f2h(float f) { return (unsigned)__half_as_ushort(__float2half_rn(f)); }
-
-template <>
-struct Vec<__half, 4> {
-    using raw = uint2;  // x: cells 0,1 (low half first); y: cells 2,3
-    static __device__ __forceinline__ raw ld(const __half *p) { return __ldg(reinterpret_cast<const uint2 *>(p)); }
-    static __device__ __forceinline__ float cell(raw v, int j) { return h2f(j < 2 ? v.x : v.y, j & 1); }
-    static __device__ __forceinline__ void put(raw &v, int j, float f)
-    {
-        unsigned &w = j < 2 ? v.x : v.y;
-        w = (j & 1) ? ((w & 0xffffu) | (f2h(f) << 16)) : ((w & 0xffff0000u) | f2h(f));
-    }
-    static __device__ __forceinline__ void st(__half *p, raw v) { __stcs(reinterpret_cast<uint2 *>(p), v); }
-    static __device__ __forceinline__ void st1(__half *p, raw v, int j)
-    {
-        const unsigned w = j < 2 ? v.x : v.y;
-        __stcs(p + j, __ushort_as_half((unsigned short)((j & 1) ? w >> 16 : w & 0xffffu)));
-    }
-    // (x-1, x, x+1, x+2)
-    static __device__ __forceinline__ raw shift_left(raw cur, const __half *xl, bool side)
-    {
-        unsigned l = __shfl_up_sync(0xffffffffu, cur.y, 1);
-        if (side) l = (unsigned)__half_as_ushort(__ldg(xl)) << 16;
-        return make_uint2(__byte_perm(l, cur.x, 0x5432), __byte_perm(cur.x, cur.y, 0x5432));
-    }
-    // (x+1, x+2, x+3, x+4); xr = x+4 when read directly
-    static __device__ __forceinline__ raw shift_right(raw cur, const __half *xr, bool side)
-    {
-        unsigned r = __shfl_down_sync(0xffffffffu, cur.x, 1);
-        if (side) r = (unsigned)__half_as_ushort(__ldg(xr));
-        return make_uint2(__byte_perm(cur.x, cur.y, 0x5432), __byte_perm(cur.y, r, 0x5432));
-    }
-};
 
 template <>
 struct Vec<__half, 2> {
@@ -372,7 +336,7 @@ struct Vec<__half, 2> {
         return f;
     }
     // both halves in FP32 (.x the first cell)
-    static __device__ __forceinline__ float2 pair(raw v)
+    static __device__ __forceinline__ float2 pair(raw v, int = 0)
     {
         float2 f;
         asm("{.reg .b16 lo, hi; mov.b32 {lo, hi}, %2; cvt.f32.f16 %0, lo; cvt.f32.f16 %1, hi;}"
@@ -417,6 +381,8 @@ struct Vec<__half, 2> {
         asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(v) : "f"(hi), "f"(lo), "r"(rb));
         return v;
     }
+    static __device__ __forceinline__ void set_pair(raw &v, int, float lo, float hi) { v = pack(lo, hi); }
+    static __device__ __forceinline__ void set_pair_rs(raw &v, int, float lo, float hi, unsigned rb) { v = pack_rs(lo, hi, rb); }
     static __device__ __forceinline__ void st(__half *p, raw v) { __stcs(reinterpret_cast<unsigned *>(p), v); }
     static __device__ __forceinline__ void st1(__half *p, raw v, int j)
     {
@@ -456,12 +422,66 @@ struct Vec<__half, 2> {
     }
 };
 
-// cells per lane: 2 for both storages (FP32 8-byte pairs, FP16 4-byte pairs);
-// Vec<__half, 4> (8-byte quads) is kept for lattices where its 128-register
-// footprint pays off.
-template <typename S>
-struct VecOf {
-    static constexpr int CPL = 2;
+template <>
+struct Vec<__half, 4> {
+    using raw = uint2;  // x: cells 0, 1 (low half first); y: cells 2, 3
+    // 8-byte read-only load with the 256-byte L2 fetch (a warp reads a 256 B row piece)
+    static __device__ __forceinline__ raw ld(const __half *p)
+    {
+        raw v;
+        asm volatile("ld.global.nc.L2::256B.v2.b32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+        return v;
+    }
+    static __device__ __forceinline__ unsigned word(raw v, int j) { return j < 2 ? v.x : v.y; }
+    static __device__ __forceinline__ float cell(raw v, int j) { return Vec<__half, 2>::cell(word(v, j), j & 1); }
+    // cells 2k and 2k + 1 in FP32
+    static __device__ __forceinline__ float2 pair(raw v, int k) { return Vec<__half, 2>::pair(k ? v.y : v.x); }
+    static __device__ __forceinline__ float add_h(raw v, int j, float c) { return Vec<__half, 2>::add_h(word(v, j), j & 1, c); }
+    static __device__ __forceinline__ float sub_h(raw v, int j, float c) { return Vec<__half, 2>::sub_h(word(v, j), j & 1, c); }
+    // cells 2k, 2k + 1 <- lo, hi (round to nearest, or stochastic rounding with bits rb)
+    static __device__ __forceinline__ void set_pair(raw &v, int k, float lo, float hi)
+    {
+        (k ? v.y : v.x) = Vec<__half, 2>::pack(lo, hi);
+    }
+    static __device__ __forceinline__ void set_pair_rs(raw &v, int k, float lo, float hi, unsigned rb)
+    {
+        (k ? v.y : v.x) = Vec<__half, 2>::pack_rs(lo, hi, rb);
+    }
+    static __device__ __forceinline__ void st(__half *p, raw v) { __stcs(reinterpret_cast<uint2 *>(p), v); }
+    // cell j at p + j
+    static __device__ __forceinline__ void st1(__half *p, raw v, int j) { Vec<__half, 2>::st1(p + (j & 2), word(v, j), j & 1); }
+    // cells 1 and 2 as one aligned pair at p
+    static __device__ __forceinline__ void st_mid(__half *p, raw v)
+    {
+        __stcs(reinterpret_cast<unsigned *>(p), __byte_perm(v.x, v.y, 0x5432));
+    }
+    // (x-1 .. x+2) and (x+1 .. x+4) with the missing value read as one binary16
+    // beside the quad (row = element x; the caller keeps row[-1] and row[4]
+    // inside the allocation)
+    static __device__ __forceinline__ raw halo_left(raw cur, const __half *row)
+    {
+        const unsigned h = __half_as_ushort(__ldg(row - 1));
+        return make_uint2(__byte_perm(h, cur.x, 0x5410), __byte_perm(cur.x, cur.y, 0x5432));
+    }
+    static __device__ __forceinline__ raw halo_right(raw cur, const __half *row)
+    {
+        const unsigned h = __half_as_ushort(__ldg(row + 4));
+        return make_uint2(__byte_perm(cur.x, cur.y, 0x5432), __byte_perm(cur.y, h, 0x5432));
+    }
+    // (x-1 .. x+2) from the left lane's cell 3 and ours; xl = x-1 when read directly
+    static __device__ __forceinline__ raw shift_left(raw cur, const __half *xl, bool side)
+    {
+        unsigned l = __shfl_up_sync(0xffffffffu, cur.y, 1);
+        if (side) l = (unsigned)__half_as_ushort(__ldg(xl)) << 16;
+        return make_uint2(__byte_perm(l, cur.x, 0x5432), __byte_perm(cur.x, cur.y, 0x5432));
+    }
+    // (x+1 .. x+4) from ours and the right lane's cell 0; xr = x+4 when read directly
+    static __device__ __forceinline__ raw shift_right(raw cur, const __half *xr, bool side)
+    {
+        unsigned r = __shfl_down_sync(0xffffffffu, cur.x, 1);
+        if (side) r = (unsigned)__half_as_ushort(__ldg(xr));
+        return make_uint2(__byte_perm(cur.x, cur.y, 0x5432), __byte_perm(cur.y, r, 0x5432));
+    }
 };
 
 // One vector column (CPL 32 cells wide) at row y over the planes z = zb,
@@ -481,22 +501,22 @@ struct VecOf {
 // c_x < 0 at x = nx-1, planes 2..14) and are the unknowns that the inlet and
 // outlet rebuilds replace.
 // Returns the thread's sum of rho - 1.
-template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP, bool H16, int MODE, bool SR>
-__device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX * VecOf<S>::CPL], int x0, int y,
-                                          int zb, int ze, int zs)
+template <typename S, int CPL, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP, bool H16, int MODE, bool SR>
+__device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX * CPL], int x0, int y, int zb,
+                                          int ze, int zs)
 {
-    constexpr int CPL = VecOf<S>::CPL;
+    static_assert(CPL == 2 || (CPL == 4 && sizeof(S) == 2), "pairs, or binary16 quads");
     using V = Vec<S, CPL>;
     using raw = typename V::raw;
-    // binary16 pairs, regularized collision: pair sums by mixed-precision adds
-    constexpr bool MIXED = REG && sizeof(S) == 2 && CPL == 2;
-    // binary16 pairs, regularized unforced collision: both cells in packed
-    // FP32 (lbm_pair.cuh) wherever the warp's 64 cells hold no inlet or outlet
-    // node; the warps that do, the other collisions and FP32 storage (whose
-    // step is bound by memory either way) update cell by cell.  A warp's chunk
-    // is the same in every kernel and tile, so each cell always takes the
-    // same form.
-    constexpr bool PACKED = REG && !FORCE && sizeof(S) == 2 && CPL == 2;
+    // binary16, regularized collision: pair sums by mixed-precision adds
+    constexpr bool MIXED = REG && sizeof(S) == 2;
+    // binary16, regularized unforced collision: the lane's cells go through
+    // the collision two at a time in packed FP32 (lbm_pair.cuh) wherever the
+    // warp's 32 CPL cells hold no inlet or outlet node; the warps that do, the
+    // other collisions and FP32 storage (whose step is bound by memory either
+    // way) update cell by cell.  A warp's chunk is the same in every kernel and
+    // tile, so each cell always takes the same form.
+    constexpr bool PACKED = REG && !FORCE && sizeof(S) == 2;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int nxy = nx * ny;
     const int lane = threadIdx.x, wi = threadIdx.y;
@@ -590,36 +610,42 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
             else if (cx > 0) v[i] = V::shift_left(cur, sbase + (rbase + xl), side_l && !(inout && x == 0));
             else v[i] = V::shift_right(cur, sbase + (rbase + xr), side_r && !(inout && x + CPL == nx));
         }
-        const unsigned seed = SR ? sr_seed(here, tmix) : 0u;
+        // stochastic rounding: the bits of a pair's conversion depend on the
+        // pair's first cell, so pairs and quads round a lattice alike
+        auto seed_of = [&](int k) { return SR ? sr_seed(here + 2 * k, tmix) : 0u; };
         if (PACKED && !node_warp) {
-            // both cells of the lane at once (packed FP32 pairs)
-            float2 nuf = make_float2(1.0f, 1.0f);
-            if (SP && active) nuf = __ldg(reinterpret_cast<const float2 *>(a.spf + x));
-            const PairMoments m = pair_moments([&](int i) { return V::pair(v[i]); });
-            float2 drho, ux, uy, uz;
-            collide_pair<SP>(m, tau0, kq, nuf, [&](int i, float2 r) {
-                if constexpr (SR) v[i] = V::pack_rs(r.x, r.y, sr_bits(seed, i));
-                else v[i] = V::pack(r.x, r.y);
-            }, drho, ux, uy, uz);
-            if (active) {
-                if (STATS) {
-                    constexpr int L = BX * CPL;
+            // the lane's cells two at a time (packed FP32 pairs)
 #pragma unroll
-                    for (int j = 0; j < CPL; ++j) {
-                        float *sp = &sacc[wi][0][CPL * lane + j];
-                        const float vx = j ? ux.y : ux.x, vy = j ? uy.y : uy.x, vz = j ? uz.y : uz.x;
-                        sp[0 * L] += vx; sp[1 * L] += vy; sp[2 * L] += vz;
-                        sp[3 * L] = __fmaf_rn(vx, vx, sp[3 * L]); sp[4 * L] = __fmaf_rn(vy, vy, sp[4 * L]);
-                        sp[5 * L] = __fmaf_rn(vz, vz, sp[5 * L]); sp[6 * L] = __fmaf_rn(vx, vy, sp[6 * L]);
-                        sp[7 * L] = __fmaf_rn(vx, vz, sp[7 * L]); sp[8 * L] = __fmaf_rn(vy, vz, sp[8 * L]);
+            for (int k = 0; k < CPL / 2; ++k) {
+                float2 nuf = make_float2(1.0f, 1.0f);
+                if (SP && active) nuf = __ldg(reinterpret_cast<const float2 *>(a.spf + x + 2 * k));
+                const unsigned seed = seed_of(k);
+                const PairMoments m = pair_moments([&](int i) { return V::pair(v[i], k); });
+                float2 drho, ux, uy, uz;
+                collide_pair<SP>(m, tau0, kq, nuf, [&](int i, float2 r) {
+                    if constexpr (SR) V::set_pair_rs(v[i], k, r.x, r.y, sr_bits(seed, i));
+                    else V::set_pair(v[i], k, r.x, r.y);
+                }, drho, ux, uy, uz);
+                if (active) {
+                    if (STATS) {
+                        constexpr int L = BX * CPL;
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            float *sp = &sacc[wi][0][CPL * lane + 2 * k + j];
+                            const float vx = j ? ux.y : ux.x, vy = j ? uy.y : uy.x, vz = j ? uz.y : uz.x;
+                            sp[0 * L] += vx; sp[1 * L] += vy; sp[2 * L] += vz;
+                            sp[3 * L] = __fmaf_rn(vx, vx, sp[3 * L]); sp[4 * L] = __fmaf_rn(vy, vy, sp[4 * L]);
+                            sp[5 * L] = __fmaf_rn(vz, vz, sp[5 * L]); sp[6 * L] = __fmaf_rn(vx, vy, sp[6 * L]);
+                            sp[7 * L] = __fmaf_rn(vx, vz, sp[7 * L]); sp[8 * L] = __fmaf_rn(vy, vz, sp[8 * L]);
+                        }
                     }
+                    sdr += drho.x;
+                    sdr += drho.y;
                 }
-                sdr += drho.x;
-                sdr += drho.y;
             }
         } else {
         float upx = 0.f, upy = 0.f, upz = 0.f;  // velocity of the lane's previous cell
-        float gp[CPL == 2 ? Q : 1];             // first cell's results (pairs)
+        float gp[Q];                            // results of the pair's first cell
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
             float g[Q];
@@ -681,16 +707,14 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
             upx = ux;
             upy = uy;
             upz = uz;
-            if constexpr (CPL == 2) {
+            // the pair's first cell waits in FP32; the second completes the pair,
+            // which replaces the pair's (already read) inputs
+            const unsigned seed = (j & 1) ? seed_of(j >> 1) : 0u;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    if (j == 0) gp[i] = g[i];
-                    else if constexpr (SR) v[i] = V::pack_rs(gp[i], g[i], sr_bits(seed, i));
-                    else v[i] = V::pack(gp[i], g[i]);
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) V::put(v[i], j, g[i]);
+            for (int i = 0; i < Q; ++i) {
+                if ((j & 1) == 0) gp[i] = g[i];
+                else if constexpr (SR) V::set_pair_rs(v[i], j >> 1, gp[i], g[i], sr_bits(seed, i));
+                else V::set_pair(v[i], j >> 1, gp[i], g[i]);
             }
             const bool counted = active;
             if (STATS && counted) {
@@ -738,18 +762,26 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
                 if (cx == 0) {
                     V::st(tx, v[i]);
                 } else if (cx < 0) {
-                    // cell x + 1 -> x, cell x -> x - 1; the row's first cell
+                    // cells x + 1 .. x + CPL - 1 -> x .. x + CPL - 2 (quads: cells 1, 2
+                    // as one aligned pair), cell x -> x - 1; the row's first cell
                     // (lanes with x = 0 only): outside at the inlet (the own slot),
                     // wraps to x = nx - 1 when x is periodic
-                    V::st1(tx - 1, v[i], 1);
+                    if constexpr (CPL == 4) {
+                        V::st_mid(tx, v[i]);
+                        V::st1(tx - 1, v[i], 3);
+                    } else {
+                        V::st1(tx - 1, v[i], 1);
+                    }
                     if (x > 0) V::st1(tx - 1, v[i], 0);
                     else V::st1(inout ? own_slot(i) : tx + (nx - 1), v[i], 0);
                 } else {
-                    // cell x -> x + 1, cell x + 1 -> x + 2; the row's last cell
-                    // (lanes with x = nx - 2 only): outside at the outlet, wraps to 0
+                    // cells x .. x + CPL - 2 -> x + 1 .. x + CPL - 1 (quads: cells 1, 2
+                    // as one aligned pair), cell x + CPL - 1 -> x + CPL; the row's last
+                    // cell (lanes with x = nx - CPL only): outside at the outlet, wraps to 0
                     V::st1(tx + 1, v[i], 0);
-                    if (x + 2 < nx) V::st1(tx + 1, v[i], 1);
-                    else V::st1(inout ? own_slot(i) : tx - (x + 1), v[i], 1);
+                    if constexpr (CPL == 4) V::st_mid(tx + 2, v[i]);
+                    if (x + CPL < nx) V::st1(tx + 1, v[i], CPL - 1);
+                    else V::st1(inout ? own_slot(i) : tx - (x + CPL - 1), v[i], CPL - 1);
                 }
             }
         }
@@ -769,12 +801,12 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
 // H16 as in vec_loop.  STATS is chosen on the host (it knows the step
 // count); plain steps use lbm_vec_zc_kernel.
 constexpr int STAT_NW = 4;  // warps (x chunks) per sampling block
-template <typename S, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP, bool H16, int MODE, bool SR>
+template <typename S, int CPL, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP, bool H16, int MODE, bool SR>
 // (the wall rows, on the branch beside the interior launch, may take 128
-// registers so that they need no stack frame)
-__global__ void __launch_bounds__(BX *STAT_NW, YEDGE ? 4 : ((REG && !FORCE) ? 8 : 6)) lbm_vec_kernel(const StepArgs a)
+// registers so that they need no stack frame; binary16 quads take 96)
+__global__ void __launch_bounds__(BX *STAT_NW, YEDGE ? 4 : ((REG && !FORCE) ? (CPL == 4 ? 5 : 8) : 6))
+    lbm_vec_kernel(const StepArgs a)
 {
-    constexpr int CPL = VecOf<S>::CPL;
     __shared__ float sacc[STATS ? STAT_NW : 1][9][BX * CPL];  // per-thread statistics slots
     const int nx = a.nx, ny = a.ny;
     const int lane = threadIdx.x, wi = threadIdx.y;
@@ -789,7 +821,7 @@ __global__ void __launch_bounds__(BX *STAT_NW, YEDGE ? 4 : ((REG && !FORCE) ? 8 
             for (int j = 0; j < CPL; ++j) sacc[wi][q][CPL * lane + j] = 0.f;
     }
     const int zb = STATS ? blockIdx.z * STAT_GROUP : 0;
-    const float sdr = vec_loop<S, REG, FORCE, STATS, YEDGE, SP, H16, MODE, SR>(
+    const float sdr = vec_loop<S, CPL, REG, FORCE, STATS, YEDGE, SP, H16, MODE, SR>(
         a, sacc, x0, y, zb, STATS ? min(zb + STAT_GROUP, a.nz) : a.nz, 1);
     if (STATS) {
         // each thread wrote only its own slots: no barrier
@@ -814,22 +846,24 @@ __global__ void __launch_bounds__(BX *STAT_NW, YEDGE ? 4 : ((REG && !FORCE) ? 8 
 // short blocks instead of one block per z column keep the last wave of the
 // grid small.  LAYOUT 0: 8 warps on one 64-cell x chunk, warp w taking the
 // planes w, w + 8, ... of the chunk; LAYOUT 1: 4 warps on 4 consecutive x
-// chunks (256 cells), all walking the chunk's planes together.  The regularized
-// unforced interior variants fit 64 registers (32 warps per SM); BGK, forced
-// and wall-row ones get 80 (24 warps per SM).
-template <int LAYOUT, bool LEAN>
+// chunks (256 cells), all walking the chunk's planes together (binary16
+// quads: 128-cell chunks).  The regularized unforced interior variants fit 64
+// registers with pairs (32 warps per SM) and 96 with quads (20 warps per SM:
+// with 8-byte row pieces those warps keep as many bytes in flight as FP32);
+// BGK, forced and wall-row ones get 80 with pairs (24 warps per SM) and 128
+// with quads.
+template <int LAYOUT, bool LEAN, int CPL = 2>
 struct ZcShape {
     static constexpr int NW = LAYOUT == 0 ? BZ : 4;  // warps per block
-    static constexpr int MINB = (LEAN ? 32 : 24) / NW;  // resident blocks per SM
+    static constexpr int MINB = (CPL == 4 ? (LEAN ? 20 : 16) : (LEAN ? 32 : 24)) / NW;  // resident blocks per SM
 };
 
-template <typename S, bool REG, bool FORCE, int LAYOUT, bool YEDGE, bool SP, bool H16, int MODE, bool SR>
-__global__ void __launch_bounds__(BX *ZcShape<LAYOUT, REG && !FORCE && !YEDGE>::NW,
-                                  ZcShape<LAYOUT, REG && !FORCE && !YEDGE>::MINB)
+template <typename S, int CPL, bool REG, bool FORCE, int LAYOUT, bool YEDGE, bool SP, bool H16, int MODE, bool SR>
+__global__ void __launch_bounds__(BX *ZcShape<LAYOUT, REG && !FORCE && !YEDGE, CPL>::NW,
+                                  ZcShape<LAYOUT, REG && !FORCE && !YEDGE, CPL>::MINB)
     lbm_vec_zc_kernel(const StepArgs a)
 {
-    constexpr int CPL = VecOf<S>::CPL;
-    constexpr int NW = ZcShape<LAYOUT, REG && !FORCE && !YEDGE>::NW;
+    constexpr int NW = ZcShape<LAYOUT, REG && !FORCE && !YEDGE, CPL>::NW;
     const int wi = threadIdx.y;
     const int y = YEDGE ? (blockIdx.y == 0 ? 0 : a.ny - 1) : blockIdx.y + 1;
     const int zc0 = YEDGE ? a.tile_wall_zc : a.tile_zc;
@@ -839,9 +873,9 @@ __global__ void __launch_bounds__(BX *ZcShape<LAYOUT, REG && !FORCE && !YEDGE>::
     const bool do_check = a.check_every > 0 && ((t + 1) % a.check_every) == 0;
     float sdr;
     if (LAYOUT == 0)
-        sdr = vec_loop<S, REG, FORCE, false, YEDGE, SP, H16, MODE, SR>(a, nullptr, BX * CPL * blockIdx.x, y, zb + wi, ze, NW);
+        sdr = vec_loop<S, CPL, REG, FORCE, false, YEDGE, SP, H16, MODE, SR>(a, nullptr, BX * CPL * blockIdx.x, y, zb + wi, ze, NW);
     else
-        sdr = vec_loop<S, REG, FORCE, false, YEDGE, SP, H16, MODE, SR>(a, nullptr, BX * CPL * (NW * blockIdx.x + wi), y, zb, ze, 1);
+        sdr = vec_loop<S, CPL, REG, FORCE, false, YEDGE, SP, H16, MODE, SR>(a, nullptr, BX * CPL * (NW * blockIdx.x + wi), y, zb, ze, 1);
     if (do_check) mass_finish<BX * NW>(a, sdr);
     if (YEDGE && a.bump_t && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && wi == 0)
         a.ctl->t[a.parity ^ 1] = t + 1;
@@ -879,9 +913,12 @@ __global__ void __launch_bounds__(BX *BZ, 2) lbm_edge_kernel(const StepArgs a)
 //  scalar split: interior kernel (one cell per thread) on the
 //                32-wide chunks [1, nxc-1) of rows 1..ny-2, edge kernel on the
 //                rest.
+// binary16 regularized unforced lattices take quads (four cells per lane)
+// when the rows split into whole quads
+static inline bool quads_fit(int nx) { return nx % 4 == 0 && nx >= 8; }
+
 struct Split {
     bool vec;
-    int nxv;                   // vector chunks per row
     int il, ir, gx, gy;        // scalar split interior
     int n_edge;
 };
@@ -895,10 +932,7 @@ static Split split_of(const StepArgs &a, int cpl)
     // its lattice conditions), so it ignores the interior override
     sp.vec = (a.aa || a.interior == 0 || a.interior == 2) && nx % cpl == 0 && nx >= 2 * cpl &&
              19.0 * nx * ny * nz < 4294967296.0 && (a.bc_x != 0 || nx >= 3);
-    if (sp.vec) {
-        sp.nxv = (nx + BX * cpl - 1) / (BX * cpl);
-        return sp;
-    }
+    if (sp.vec) return sp;
     if (nxc >= 3 && ny >= 3) {
         sp.il = 1;
         sp.ir = nxc - 1;
@@ -911,13 +945,14 @@ static Split split_of(const StepArgs &a, int cpl)
 }
 
 // Vector split of one pass in streaming mode MODE.
-template <typename S, bool REG, bool FORCE, bool SP, int MODE, bool SR>
-static void launch_vec(StepArgs a, const Split &sp, bool stats, cudaStream_t s, cudaStream_t side)
+template <typename S, int CPL, bool REG, bool FORCE, bool SP, int MODE, bool SR>
+static void launch_vec(StepArgs a, bool stats, cudaStream_t s, cudaStream_t side)
 {
     const dim3 block(BX, BZ);
     {
-        constexpr int cpl = VecOf<S>::CPL;
+        constexpr int cpl = CPL;
         const int nx = a.nx, ny = a.ny;
+        const int nxv = (nx + BX * cpl - 1) / (BX * cpl);  // vector chunks per row
         const int rows_in = ny > 2 ? ny - 2 : 0, rows_edge = ny >= 2 ? 2 : 1;
         const int nz = a.nz;
         // grids: sampling steps take fixed groups of STAT_GROUP planes (their
@@ -931,17 +966,17 @@ static void launch_vec(StepArgs a, const Split &sp, bool stats, cudaStream_t s, 
         if (!stats) {
             const int zc = a.tile_zc > 0 ? a.tile_zc : nz, wzc = a.tile_wall_zc > 0 ? a.tile_wall_zc : nz;
             if (a.tile_layout == 1) {
-                constexpr int W = ZcShape<1, true>::NW;
+                constexpr int W = ZcShape<1, true, CPL>::NW;
                 gi = dim3((nx + BX * cpl * W - 1) / (BX * cpl * W), rows_in, (nz + zc - 1) / zc);
                 bi = dim3(BX, W);
             } else {
-                gi = dim3(sp.nxv, rows_in, (nz + zc - 1) / zc);
+                gi = dim3(nxv, rows_in, (nz + zc - 1) / zc);
             }
-            ge = dim3(sp.nxv, rows_edge, (nz + wzc - 1) / wzc);
+            ge = dim3(nxv, rows_edge, (nz + wzc - 1) / wzc);
         }
         const int n_in = rows_in > 0 ? (int)(gi.x * gi.y * gi.z) : 0;
         const int n_edge = (int)(ge.x * ge.y * ge.z);
-        // binary16 pairs in an inlet/outlet lattice: x halo by 2-byte loads
+        // binary16 in an inlet/outlet lattice: x halo by 2-byte loads
         // (the local in-place step reads no x neighbour)
         constexpr bool H = sizeof(S) == 2 && MODE != AA_LOCAL;
         const bool h16 = H && a.bc_x == 0;
@@ -951,17 +986,17 @@ static void launch_vec(StepArgs a, const Split &sp, bool stats, cudaStream_t s, 
         ae.slot_base = n_in;
         ae.bump_t = 1;
         if (n_in > 0) {
-            if (stats && h16) lbm_vec_kernel<S, REG, FORCE, true, false, SP, H, MODE, SR><<<gi, bs, 0, s>>>(ai);
-            else if (stats) lbm_vec_kernel<S, REG, FORCE, true, false, SP, false, MODE, SR><<<gi, bs, 0, s>>>(ai);
-            else if (h16 && a.tile_layout == 1) lbm_vec_zc_kernel<S, REG, FORCE, 1, false, SP, H, MODE, SR><<<gi, bi, 0, s>>>(ai);
-            else if (h16) lbm_vec_zc_kernel<S, REG, FORCE, 0, false, SP, H, MODE, SR><<<gi, bi, 0, s>>>(ai);
-            else if (a.tile_layout == 1) lbm_vec_zc_kernel<S, REG, FORCE, 1, false, SP, false, MODE, SR><<<gi, bi, 0, s>>>(ai);
-            else lbm_vec_zc_kernel<S, REG, FORCE, 0, false, SP, false, MODE, SR><<<gi, bi, 0, s>>>(ai);
+            if (stats && h16) lbm_vec_kernel<S, CPL, REG, FORCE, true, false, SP, H, MODE, SR><<<gi, bs, 0, s>>>(ai);
+            else if (stats) lbm_vec_kernel<S, CPL, REG, FORCE, true, false, SP, false, MODE, SR><<<gi, bs, 0, s>>>(ai);
+            else if (h16 && a.tile_layout == 1) lbm_vec_zc_kernel<S, CPL, REG, FORCE, 1, false, SP, H, MODE, SR><<<gi, bi, 0, s>>>(ai);
+            else if (h16) lbm_vec_zc_kernel<S, CPL, REG, FORCE, 0, false, SP, H, MODE, SR><<<gi, bi, 0, s>>>(ai);
+            else if (a.tile_layout == 1) lbm_vec_zc_kernel<S, CPL, REG, FORCE, 1, false, SP, false, MODE, SR><<<gi, bi, 0, s>>>(ai);
+            else lbm_vec_zc_kernel<S, CPL, REG, FORCE, 0, false, SP, false, MODE, SR><<<gi, bi, 0, s>>>(ai);
         }
-        if (stats && h16) lbm_vec_kernel<S, REG, FORCE, true, true, SP, H, MODE, SR><<<ge, bs, 0, side>>>(ae);
-        else if (stats) lbm_vec_kernel<S, REG, FORCE, true, true, SP, false, MODE, SR><<<ge, bs, 0, side>>>(ae);
-        else if (h16) lbm_vec_zc_kernel<S, REG, FORCE, 0, true, SP, H, MODE, SR><<<ge, block, 0, side>>>(ae);
-        else lbm_vec_zc_kernel<S, REG, FORCE, 0, true, SP, false, MODE, SR><<<ge, block, 0, side>>>(ae);
+        if (stats && h16) lbm_vec_kernel<S, CPL, REG, FORCE, true, true, SP, H, MODE, SR><<<ge, bs, 0, side>>>(ae);
+        else if (stats) lbm_vec_kernel<S, CPL, REG, FORCE, true, true, SP, false, MODE, SR><<<ge, bs, 0, side>>>(ae);
+        else if (h16) lbm_vec_zc_kernel<S, CPL, REG, FORCE, 0, true, SP, H, MODE, SR><<<ge, block, 0, side>>>(ae);
+        else lbm_vec_zc_kernel<S, CPL, REG, FORCE, 0, true, SP, false, MODE, SR><<<ge, block, 0, side>>>(ae);
     }
 }
 
@@ -972,10 +1007,21 @@ static bool launch_forced(StepArgs a, const Split &sp, bool stats, cudaStream_t 
 {
     const dim3 block(BX, BZ);
     if (sp.vec) {
+        // binary16, regularized unforced, rows of whole quads: four cells per lane
+        constexpr bool QUAD = sizeof(S) == 2 && REG && !FORCE;
         // in place: steps with even index shift, steps with odd index stay local
-        if (!a.aa) launch_vec<S, REG, FORCE, SP, PULL, SR>(a, sp, stats, s, side);
-        else if (a.parity == 0) launch_vec<S, REG, FORCE, SP, AA_SHIFT, SR>(a, sp, stats, s, side);
-        else launch_vec<S, REG, FORCE, SP, AA_LOCAL, SR>(a, sp, stats, s, side);
+        const int mode = !a.aa ? PULL : (a.parity == 0 ? AA_SHIFT : AA_LOCAL);
+        if (QUAD && quads_fit(a.nx)) {
+            if constexpr (QUAD) {
+                if (mode == PULL) launch_vec<S, 4, REG, FORCE, SP, PULL, SR>(a, stats, s, side);
+                else if (mode == AA_SHIFT) launch_vec<S, 4, REG, FORCE, SP, AA_SHIFT, SR>(a, stats, s, side);
+                else launch_vec<S, 4, REG, FORCE, SP, AA_LOCAL, SR>(a, stats, s, side);
+            }
+        } else {
+            if (mode == PULL) launch_vec<S, 2, REG, FORCE, SP, PULL, SR>(a, stats, s, side);
+            else if (mode == AA_SHIFT) launch_vec<S, 2, REG, FORCE, SP, AA_SHIFT, SR>(a, stats, s, side);
+            else launch_vec<S, 2, REG, FORCE, SP, AA_LOCAL, SR>(a, stats, s, side);
+        }
         return stats;
     }
     const int n_in = sp.gy > 0 ? sp.gx * sp.gy : 0;
@@ -997,7 +1043,7 @@ static bool launch_forced(StepArgs a, const Split &sp, bool stats, cudaStream_t 
 template <typename S, bool REG, bool SR = false>
 bool launch_typed(const StepArgs &a0, bool stats, cudaStream_t s, cudaStream_t side)
 {
-    const Split sp = split_of(a0, VecOf<S>::CPL);
+    const Split sp = split_of(a0, 2);
     StepArgs a = a0;
     a.bump_t = 0;
     // the sponge is only compiled for unforced lattices (the host refuses a sponge with a force)
