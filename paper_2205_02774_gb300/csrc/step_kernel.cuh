@@ -791,8 +791,8 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
 
 // Sampling-step vector kernel over all x of rows 1..ny-2 (YEDGE false) or of
 // rows 0 and ny-1 (YEDGE true; that launch also advances the device step
-// counter).  Block (4 consecutive 64-cell x chunks, row, group of STAT_GROUP
-// z planes); each warp walks the group's planes in order for its own chunk
+// counter).  Block (4 consecutive 64-cell x chunks, or one 128-cell quad
+// chunk, row, group of STAT_GROUP z planes); each warp walks the group's planes in order for its own chunk
 // (the plain kernel's layout 1), its lanes adding the velocity moments of
 // their cells to private shared-memory slots, and writes the group's FP32
 // sums per (x, y) to the group's slot of a.stat_part; stats_reduce_kernel
@@ -800,13 +800,20 @@ __device__ __forceinline__ float vec_loop(const StepArgs &a, float (*sacc)[9][BX
 // the statistics are deterministic and independent of the launch tile.
 // H16 as in vec_loop.  STATS is chosen on the host (it knows the step
 // count); plain steps use lbm_vec_zc_kernel.
-constexpr int STAT_NW = 4;  // warps (x chunks) per sampling block
+// warps (x chunks) per block of the layout-1 and sampling kernels: 4 with
+// pairs (256 cells), one with quads (128 cells: wider quad blocks leave warps
+// idle on rows that are not a multiple of their width, e.g. a quarter of them
+// on 768-cell rows, and were no faster on 1536-cell rows)
+constexpr int QUAD_NW = 1;
+template <int CPL>
+constexpr int chunk_warps() { return CPL == 4 ? QUAD_NW : 4; }
 template <typename S, int CPL, bool REG, bool FORCE, bool STATS, bool YEDGE, bool SP, bool H16, int MODE, bool SR>
 // (the wall rows, on the branch beside the interior launch, may take 128
 // registers so that they need no stack frame; binary16 quads take 96)
-__global__ void __launch_bounds__(BX *STAT_NW, YEDGE ? 4 : ((REG && !FORCE) ? (CPL == 4 ? 5 : 8) : 6))
+__global__ void __launch_bounds__(BX *chunk_warps<CPL>(), (YEDGE ? 16 : ((REG && !FORCE) ? (CPL == 4 ? 20 : 32) : 24)) / chunk_warps<CPL>())
     lbm_vec_kernel(const StepArgs a)
 {
+    constexpr int STAT_NW = chunk_warps<CPL>();
     __shared__ float sacc[STATS ? STAT_NW : 1][9][BX * CPL];  // per-thread statistics slots
     const int nx = a.nx, ny = a.ny;
     const int lane = threadIdx.x, wi = threadIdx.y;
@@ -847,14 +854,14 @@ __global__ void __launch_bounds__(BX *STAT_NW, YEDGE ? 4 : ((REG && !FORCE) ? (C
 // grid small.  LAYOUT 0: 8 warps on one 64-cell x chunk, warp w taking the
 // planes w, w + 8, ... of the chunk; LAYOUT 1: 4 warps on 4 consecutive x
 // chunks (256 cells), all walking the chunk's planes together (binary16
-// quads: 128-cell chunks).  The regularized unforced interior variants fit 64
+// quads: one warp on one 128-cell chunk).  The regularized unforced interior variants fit 64
 // registers with pairs (32 warps per SM) and 96 with quads (20 warps per SM:
 // with 8-byte row pieces those warps keep as many bytes in flight as FP32);
 // BGK, forced and wall-row ones get 80 with pairs (24 warps per SM) and 128
 // with quads.
 template <int LAYOUT, bool LEAN, int CPL = 2>
 struct ZcShape {
-    static constexpr int NW = LAYOUT == 0 ? BZ : 4;  // warps per block
+    static constexpr int NW = LAYOUT == 0 ? BZ : chunk_warps<CPL>();  // warps per block
     static constexpr int MINB = (CPL == 4 ? (LEAN ? 20 : 16) : (LEAN ? 32 : 24)) / NW;  // resident blocks per SM
 };
 
@@ -959,6 +966,7 @@ static void launch_vec(StepArgs a, bool stats, cudaStream_t s, cudaStream_t side
         // sums go to a.stat_part and are reduced after the pass); plain steps
         // take the tile's z chunks
         const int groups = (nz + STAT_GROUP - 1) / STAT_GROUP;
+        constexpr int STAT_NW = chunk_warps<CPL>();
         const int nxs = (nx + BX * cpl * STAT_NW - 1) / (BX * cpl * STAT_NW);  // sampling blocks along x
         dim3 gi(nxs, rows_in, groups), ge(nxs, rows_edge, groups);
         const dim3 bs(BX, STAT_NW);
