@@ -93,6 +93,9 @@ struct MassArgs {
 cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stats,
                         cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join,
                         const InletArgs *inlet = nullptr);
+// binary16 regularized unforced lattices take quads (four cells per lane)
+// when the rows split into whole quads
+inline bool quads_fit(int nx) { return nx % 4 == 0 && nx >= 8; }
 cudaError_t launch_inlet(const InletArgs &a, cudaStream_t s);
 // FP64 Cholesky factor of the lattice-unit Reynolds stress per inlet node (setup)
 cudaError_t launch_setup_nodes(int ny, const double *R6, float *a6, cudaStream_t s);

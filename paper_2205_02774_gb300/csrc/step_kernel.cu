@@ -69,8 +69,13 @@ cudaError_t launch_step(const StepArgs &a, int storage, int collision, bool stat
     }
     cudaStream_t es = forked ? side : s;
     // the inlet kernel writes the plane of the next step, which nothing in
-    // this pass reads, so it runs on the branch beside the interior
-    if (inlet && (e = launch_inlet(*inlet, es)) != cudaSuccess) return e;
+    // this pass reads, so it runs on the branch beside the interior; beside a
+    // quad interior (96-register warps filling the SMs' registers) its
+    // 256-thread blocks waited for room and the step ran slower than with the
+    // inlet ahead of the pass (FP16-SR 1.813 against 1.771 ms on 1536x256x384),
+    // so there it goes first on the main stream
+    const bool quad = storage != 0 && collision == 0 && !a.has_force && quads_fit(a.nx);
+    if (inlet && (e = launch_inlet(*inlet, quad ? s : es)) != cudaSuccess) return e;
     bool reduce = false;
     if (storage == 0) {
         if (collision == 0) reduce = launch_f32_reg(a, stats, s, es);

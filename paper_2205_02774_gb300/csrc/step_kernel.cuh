@@ -920,10 +920,6 @@ __global__ void __launch_bounds__(BX *BZ, 2) lbm_edge_kernel(const StepArgs a)
 //  scalar split: interior kernel (one cell per thread) on the
 //                32-wide chunks [1, nxc-1) of rows 1..ny-2, edge kernel on the
 //                rest.
-// binary16 regularized unforced lattices take quads (four cells per lane)
-// when the rows split into whole quads
-static inline bool quads_fit(int nx) { return nx % 4 == 0 && nx >= 8; }
-
 struct Split {
     bool vec;
     int il, ir, gx, gy;        // scalar split interior
