@@ -30,7 +30,8 @@ def _spacing(vals):
 
 @pytest.mark.parametrize("dims,kw", [((64, 32, 32), dict()), ((101, 5, 7), dict()),
                                      ((130, 6, 5), dict(bc_x="periodic", force=(2e-5, 0.0, 1e-5))),
-                                     ((66, 10, 7), dict(streaming="aa"))])
+                                     ((66, 10, 7), dict(streaming="aa")), ((66, 10, 7), dict()),
+                                     ((136, 6, 5), dict(bc_x="periodic")), ((136, 6, 5), dict(bc_x="periodic", streaming="aa"))])
 def test_fp16sr_single_step_within_one_spacing(dims, kw):
     nx, ny, nz = dims
     c = SMALL.with_(nx=nx, ny=ny, nz=nz, stats_every=0, storage="fp16sr", **kw)

@@ -62,6 +62,9 @@ def _same(a, b):
     ((260, 6, 5), dict(storage="fp16s", stats_every=1)),                          # 2-byte x halo, sampling every step
     ((96, 12, 18), dict(sponge_len=10.0)),
     ((4, 3, 2), dict(n_modes=7)),                                                 # smallest in-place lattice
+    ((136, 6, 5), dict(storage="fp16sr", bc_x="periodic")),                       # quads, shuffled x halo
+    ((200, 6, 5), dict(storage="fp16s", stats_every=2)),                          # quads, ragged last chunk
+    ((8, 4, 3), dict(storage="fp16s", n_modes=7)),                                # smallest quad lattice
 ])
 def test_inplace_bit_identical_to_pull(dims, kw):
     nx, ny, nz = dims

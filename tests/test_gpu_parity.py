@@ -157,6 +157,8 @@ def test_poiseuille_gpu(collision, lam):
     ((260, 5, 4), dict()),                                            # ragged last chunk, 2-byte x halo
     ((130, 6, 5), dict(bc_x="periodic", force=(2e-5, 0.0, 1e-5))),    # periodic x: shuffled x halo
     ((64, 8, 4), dict(bc_x="periodic", bc_y="periodic", collision="bgk")),
+    ((66, 6, 5), dict()),                                             # regularized, rows of pairs (nx = 2 mod 4)
+    ((136, 6, 5), dict(bc_x="periodic")),                             # quads with the shuffled x halo
 ])
 def test_fp16_single_step(dims, kw):
     nx, ny, nz = dims
