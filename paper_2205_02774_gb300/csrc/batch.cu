@@ -148,7 +148,6 @@ int capture_block(stg_batch *b)
         b->g = nullptr;
         return bcuda(b, e, "cudaGraphInstantiate");
     }
-    BCK(cudaGraphUpload(b->g, b->stream));  // the first replay then costs no more than later ones
     b->t_cap.resize(b->m.size());
     for (size_t d = 0; d < b->m.size(); ++d) b->t_cap[d] = b->m[d]->t;
     b->dirty = false;
@@ -186,7 +185,6 @@ int capture_member(stg_batch *b, size_t d)
         b->mg[d] = nullptr;
         return bcuda(b, e, "cudaGraphInstantiate");
     }
-    BCK(cudaGraphUpload(b->mg[d], b->ms[d]));
     b->mg_t[d] = h->t;
     b->mg_B[d] = b->B;
     return STG_OK;
