@@ -265,8 +265,12 @@ int stg_lbm_info(const stg_lbm *h, stg_info *out);
  * thread blocks, never the arithmetic of a cell, so every tile gives
  * bit-identical populations and statistics (the FP64 mass of a check can
  * differ in its last bits, its block partials being summed in another order).
- *   interior_layout  0: 8 warps on one 64-cell x chunk, warps interleaved in z;
- *                    1: 4 warps on 4 consecutive 64-cell x chunks walking z together
+ *   interior_layout  0: 8 warps on one x chunk, warps interleaved in z;
+ *                    1: 4 warps on 4 consecutive x chunks walking z together
+ *                    (x chunks of 64 cells, two per lane; binary16 regularized
+ *                    unforced lattices with nx a multiple of 4 take 128-cell
+ *                    chunks, four cells per lane, and layout 1 then puts one
+ *                    warp in a block)
  *   interior_zc      z planes per block of the rows 1..ny-2 (0: the whole z column,
  *                    else >= 4)
  *   wall_zc          z planes per block of the wall rows y = 0, ny-1 (0 or >= 4)

@@ -274,11 +274,12 @@ __global__ void __launch_bounds__(BX *BZ, 4) lbm_step_kernel(const StepArgs a)
 // Several cells per lane: lane l of a warp owns CPL consecutive cells starting
 // at x = 32 CPL b + CPL l, so every population row is read and written as
 // aligned vectors (FP32 pairs: 8 B, 256 B per warp instruction; FP16 pairs:
-// 4 B, 128 B).  A pull with c_x = +1 needs the cells shifted by one: the
+// 4 B, 128 B; FP16 quads: 8 B, 256 B).  A pull with c_x = +1 needs the cells shifted by one: the
 // missing x-1 value is the top cell of the left lane's vector (warp shuffle;
 // lane 0 reads it directly, wrapping in x when x is periodic), and c_x = -1
 // mirrors this on the right.  The wide accesses keep enough bytes in flight
-// per SM to saturate HBM, which 2-byte accesses cannot.
+// per SM to saturate HBM, which 2-byte accesses cannot (and, in FP16, which
+// 4-byte pairs reach only at about 0.87 of the copy bandwidth).
 template <typename S, int CPL>
 struct Vec;
 
