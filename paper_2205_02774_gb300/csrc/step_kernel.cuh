@@ -494,8 +494,8 @@ struct Vec<__half, 4> {
 // pressure outlet, whose velocity is that of the same lane's previous cell
 // x = nx-2; their pulled values from outside the lattice are never read.
 // STATS adds the per-cell velocity sums to the block's shared-memory slots.
-// H16 (binary16 pairs, inlet/outlet in x only): the x-shifted pairs take
-// their missing value by a 2-byte load beside the pair instead of a warp
+// H16 (binary16, inlet/outlet in x only): the x-shifted pairs or quads take
+// their missing value by a 2-byte load beside the vector instead of a warp
 // shuffle.  Lane 0 of the first chunk then reads the element before its row
 // and the last lane the element after it; both lie inside the 19-plane
 // allocation (they are used only for c_x > 0 at x = 0, planes 1..13, and
